@@ -1,0 +1,241 @@
+/* dibella.h — C ABI of the GB300 seed-and-extend X-drop library (libdibella.so).
+ *
+ * The library aligns candidate long-read pairs from shared k-mer seeds with
+ * X-drop extension, the per-pair work of diBELLA (Ellis et al., ICPP 2019):
+ *   - alignment and its score: Sec. 2 ("Read-to-Read Alignment"), the
+ *     definition of a pairwise alignment of s and t and its scoring;
+ *   - X-drop: Sec. 2, the paragraph replacing full dynamic programming by a
+ *     banded search that stops once the score drops X below the best
+ *     (after Zhang et al. 2000); SeqAn's implementation in the paper;
+ *   - seeds: Sec. 2 (shared k-mers, Fig. 1) and Sec. 8 (retained k-mer
+ *     positions per overlapping pair; seed count / spacing constraints);
+ *   - the per-pair alignment stage: Sec. 9 ("Alignment").
+ * The paper fixes no recurrence, band rule or tie-break; this library
+ * implements the reading documented on dibella_xdrop_batch below.
+ *
+ * All entry points return 0 (DIBELLA_OK) on success or a negative status;
+ * on an argument error nothing has been written and no work was enqueued
+ * (dibella_pack_reads may have written part of packed_words before it finds
+ * a bad base).
+ * Thread safety: calls may run concurrently on different streams with
+ * distinct workspaces.  No entry point allocates device memory.
+ */
+#ifndef DIBELLA_H_
+#define DIBELLA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+  DIBELLA_OK = 0,
+  DIBELLA_EINVAL = -1,   /* bad scalar argument, null pointer or size       */
+  DIBELLA_EBASE = -2,    /* a read holds a byte other than A, C, G, T       */
+  DIBELLA_ENOMEM = -3,   /* caller-provided workspace too small             */
+  DIBELLA_ECUDA = -4,    /* a CUDA runtime call failed (see last_error)     */
+  DIBELLA_ETIMEOUT = -5  /* reserved: a bounded device wait ran out         */
+};
+
+/* Per-result status bits (dibella_result_t.status). */
+#define DIBELLA_RES_SEED_MISMATCH 1  /* the k seed bases are not identical   */
+#define DIBELLA_RES_INVALID_SEED 2   /* read id / seed position out of range  */
+#define DIBELLA_RES_BEST_OF_PAIR 4   /* best seed of its candidate pair       */
+#define DIBELLA_RES_BAND_OVERFLOW 8  /* band wider than the workspace allows;
+                                        score/coordinates/cells not computed  */
+
+/* X values at or above this act as "no drop-off" for reads whose path scores
+ * stay above -2^30 (every read accepted here when |gap| * length < 2^30). */
+#define DIBELLA_XDROP_INF (1 << 30)
+
+/* Limits checked on the host (EINVAL otherwise). */
+#define DIBELLA_MAX_K 32
+#define DIBELLA_MAX_SCORE 64         /* |match|, |mismatch|, |gap| <= 64      */
+#define DIBELLA_MAX_READ_LEN (1 << 24)
+
+/* ---- records ---------------------------------------------------------- */
+
+/* Linear-gap scoring (Sec. 2: matches rewarded; mismatches, insertions and
+ * deletions penalised).  Requires match > 0, mismatch <= 0, gap < 0, each of
+ * magnitude <= DIBELLA_MAX_SCORE, and 0 <= xdrop <= DIBELLA_XDROP_INF. */
+typedef struct {
+  int32_t match, mismatch, gap, xdrop;
+} dibella_scoring_t;
+
+/* One seed of a candidate pair (24 bytes).  The seed is the shared k-mer at
+ * pos_a in read_a and at pos_b in read_b, both in FORWARD coordinates;
+ * strand = 1 when the occurrences have opposite orientation, i.e. read_b is
+ * aligned reverse-complemented.  A candidate pair with several seeds is a run
+ * of consecutive records with equal (read_a, read_b); seed_id is the caller's
+ * label and is not interpreted. */
+typedef struct {
+  uint32_t read_a, read_b, pos_a, pos_b;
+  uint8_t strand;
+  uint8_t pad[3];
+  uint32_t seed_id;
+} dibella_pair_t;
+
+/* Result of one seed (40 bytes).  Coordinates are half-open; [begin_b, end_b)
+ * is in forward coordinates of read_b whatever the strand.  cells = evaluated
+ * DP cells of both extensions (the work behind GCUPS). */
+typedef struct {
+  int32_t score, score_left, score_right;
+  uint32_t begin_a, end_a, begin_b, end_b;
+  int32_t status;
+  int64_t cells;
+} dibella_result_t;
+
+/* ---- packed read store ------------------------------------------------ */
+/* Layout (Sec. 3: 2 bits per base; A=0 C=1 G=2 T=3, complement = 3 - code):
+ * 32-bit words, 16 bases per word, base q of a copy at bits 2*(q%16).
+ * The store opens with 4 zero words; then, per read r, its forward copy at
+ * word read_word_offsets[r] (a multiple of 4, i.e. 16-byte aligned) followed
+ * immediately by its reverse-complement copy; each copy takes
+ * 4*ceil(ceil(len/16)/4) words; the store closes with 4 zero words.
+ * Holding both orientations lets every extension read both sequences in
+ * ascending word order, reverse complement included. */
+
+/* Words needed for n_reads reads whose ASCII spans are given by the n_reads+1
+ * entries of ascii_offsets (non-decreasing).  Host pointers.  EINVAL on a
+ * negative count, a decreasing offset or a read longer than
+ * DIBELLA_MAX_READ_LEN. */
+int dibella_packed_words(const int64_t* ascii_offsets, int64_t n_reads,
+                         int64_t* n_words_out);
+
+/* Pack reads to the store layout above.  All pointers are HOST pointers and
+ * the caller owns every buffer: packed_words holds dibella_packed_words()
+ * words, read_word_offsets and read_lengths hold n_reads entries each.
+ * Bytes A/C/G/T (either case) are accepted; any other byte returns EBASE
+ * with *bad_index = its position in `ascii` (bad_index may be NULL).
+ * n_threads <= 0 uses every hardware thread. */
+int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t n_reads,
+                       uint32_t* packed_words, int64_t* read_word_offsets,
+                       int32_t* read_lengths, int64_t* bad_index, int32_t n_threads);
+
+/* ---- scheduling ------------------------------------------------------- */
+/* How a batch is split across the extension kernels.  Results never depend
+ * on the schedule; only speed does.  Every extension first goes to one of:
+ *   narrow  one thread per extension, band in per-thread shared memory of
+ *           narrow_band_cap cells (32, 48 or 64);
+ *   wide    one warp per extension, band in shared memory of 1024 cells;
+ * an extension whose band outgrows its kernel is re-run by the next wider
+ * one (narrow -> wide -> global-memory band sized from the workspace).
+ * An extension is routed to narrow when xdrop <= narrow_max_xdrop and
+ * min(remaining A, remaining B) <= narrow_max_len.  Work is ordered by
+ * n_buckets length buckets (longest first); bucket b holds keys below
+ * bucket_bounds[b] (ascending), the last bucket everything else. */
+#define DIBELLA_MAX_BUCKETS 8
+typedef struct {
+  int32_t narrow_max_xdrop;
+  int32_t narrow_max_len;
+  int32_t narrow_band_cap;
+  int32_t wide_blocks_per_sm;     /* 0 = occupancy maximum                   */
+  int32_t narrow_blocks_per_sm;   /* 0 = occupancy maximum                   */
+  int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
+  int32_t bucket_bounds[DIBELLA_MAX_BUCKETS];
+} dibella_schedule_t;
+
+/* The schedule used when a call passes NULL.  set() validates (EINVAL). */
+int dibella_get_default_schedule(dibella_schedule_t* out);
+int dibella_set_default_schedule(const dibella_schedule_t* sched);
+
+/* ---- X-drop batch ----------------------------------------------------- */
+
+/* Device workspace bytes for a batch of n_pairs seeds over reads of at most
+ * max_read_len bases (a bound, used to size the global-memory band of the
+ * widest kernel so that it can never overflow). */
+int dibella_xdrop_workspace_bytes(int64_t n_pairs, int32_t max_read_len,
+                                  int64_t* bytes_out);
+
+/* Align every seed record.  DEVICE pointers: packed_words, read_word_offsets,
+ * read_lengths (the store above, n_reads reads), pairs (n_pairs records),
+ * results (n_pairs records, written in input order), workspace
+ * (workspace_bytes, at least dibella_xdrop_workspace_bytes(n_pairs, ...);
+ * 256-byte aligned).  `stream` is a cudaStream_t (NULL = legacy default).
+ * `sched` may be NULL.  Asynchronous: argument errors return synchronously,
+ * per-seed problems go to result.status, and no host synchronisation or
+ * allocation happens, so the call can be captured in a CUDA graph.
+ *
+ * Semantics, per seed (Sec. 2 and Sec. 8-9, with these readings):
+ *   B' = read_b if strand = 0, else its reverse complement; the seed sits at
+ *   pos_a in A and at pos_b' = (strand ? len_b - pos_b - k : pos_b) in B'.
+ *   seed score = sum over the k seed columns of match/mismatch.
+ *   Left extension: reversed A[0,pos_a) against reversed B'[0,pos_b');
+ *   right extension: A[pos_a+k, len_a) against B'[pos_b'+k, len_b).
+ *   Each extension runs the antidiagonal X-drop DP H(i,j) = max(H(i-1,j-1) +
+ *   s(a_i,b_j), H(i-1,j) + gap, H(i,j-1) + gap) from H(0,0) = 0, where:
+ *     band of antidiagonal d = [lo(d-1), hi(d-1)+1] clipped to the matrix,
+ *       lo/hi = smallest/largest i of the LIVE cells of d-1;
+ *     a cell is live iff H >= best(<d) - xdrop; dead cells are -infinity;
+ *     best improves on a strictly larger value; on the improving
+ *       antidiagonal the live cell of smallest i wins;
+ *     the extension stops at the first antidiagonal without a live cell.
+ *   score = seed + left best + right best; begin/end from the winning cells;
+ *   cells = evaluated band cells of both extensions (antidiagonals >= 1).
+ *   Invalid seeds (read id >= n_reads, strand > 1, pos + k beyond the read)
+ *   get status DIBELLA_RES_INVALID_SEED and zero fields.  In each run of
+ *   records with equal (read_a, read_b) the valid record with the highest
+ *   score (earliest on ties) gets DIBELLA_RES_BEST_OF_PAIR.
+ * Requires 1 <= k <= DIBELLA_MAX_K and the scoring limits above. */
+int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                        const int32_t* read_lengths, int64_t n_reads,
+                        const dibella_pair_t* pairs, int64_t n_pairs, int32_t k,
+                        dibella_scoring_t scoring, dibella_result_t* results,
+                        void* workspace, int64_t workspace_bytes, void* stream,
+                        const dibella_schedule_t* sched);
+
+/* The same alignment with HOST pairs and results: copies the pairs in, runs
+ * dibella_xdrop_batch, copies the results out and synchronises `stream`.
+ * The store and the workspace are device memory; pairs/results should be
+ * pinned host memory for full copy speed.  staging is device memory of at
+ * least dibella_staging_bytes(n_pairs) bytes, 256-byte aligned. */
+int dibella_staging_bytes(int64_t n_pairs, int64_t* bytes_out);
+int dibella_xdrop_batch_host(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                             const int32_t* read_lengths, int64_t n_reads,
+                             const dibella_pair_t* host_pairs, int64_t n_pairs, int32_t k,
+                             dibella_scoring_t scoring, dibella_result_t* host_results,
+                             void* staging, void* workspace, int64_t workspace_bytes,
+                             void* stream, const dibella_schedule_t* sched);
+
+/* Baseline form of the same computation: one kernel launch per seed (one
+ * warp, left then right extension, no queues, no graph), all on `stream`.
+ * Same arguments and results as dibella_xdrop_batch; used to measure what
+ * batching buys.  Requires the same workspace. */
+int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                           const int32_t* read_lengths, int64_t n_reads,
+                           const dibella_pair_t* pairs, int64_t n_pairs, int32_t k,
+                           dibella_scoring_t scoring, dibella_result_t* results,
+                           void* workspace, int64_t workspace_bytes, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------ */
+/* Phase timing: when enabled, dibella_xdrop_batch records CUDA events on
+ * `stream` at five points: before expand, after expand/scan/scatter, after the
+ * first extend launch, after the escalation launches, after combine.  Under
+ * stream capture they are recorded as external events, so a replayed CUDA
+ * graph records them too.  dibella_phase_times() synchronises on the last
+ * event and writes up to n_max phase durations in ms (queueing, extend,
+ * escalations, combine); returns the count written.  Enable it before any
+ * capture (it creates the events). */
+int dibella_enable_phase_timing(int enable);
+int dibella_phase_times(float* ms_out, int n_max);
+
+/* Counters of the last batch run with `workspace` (synchronises `stream`):
+ * out[0] extensions routed narrow, out[1] routed wide, out[2] escalated
+ * narrow->wide, out[3] escalated wide->global, out[4] band overflows,
+ * out[5..8] evaluated cells of the extensions finished by the narrow form,
+ * the wide form of the first extend launch, the wide form of the escalation
+ * launch and the global-band form.  Returns the number written (<= n_max,
+ * at most 9), or a negative status. */
+int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
+
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char* dibella_last_error(void);
+/* Library version string. */
+const char* dibella_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIBELLA_H_ */

@@ -1,0 +1,262 @@
+"""GB300 seed-and-extend X-drop alignment (diBELLA's per-pair alignment stage).
+
+Thin ctypes binding over the C ABI of ``libdibella.so`` (declared in
+``include/dibella.h``).  Every function named ``dibella_*`` here marshals its
+arguments to the C entry point of the same name; all computation runs in the
+library's CUDA kernels.  PyTorch is used only for device memory and streams.
+There is no CPU fallback: if the library cannot be loaded, importing the
+binding's functions raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+PAIR_DTYPE = np.dtype(
+    [("read_a", "<u4"), ("read_b", "<u4"), ("pos_a", "<u4"), ("pos_b", "<u4"),
+     ("strand", "u1"), ("pad", "u1", (3,)), ("seed_id", "<u4")])
+RESULT_DTYPE = np.dtype(
+    [("score", "<i4"), ("score_left", "<i4"), ("score_right", "<i4"),
+     ("begin_a", "<u4"), ("end_a", "<u4"), ("begin_b", "<u4"), ("end_b", "<u4"),
+     ("status", "<i4"), ("cells", "<i8")])
+
+DIBELLA_OK, DIBELLA_EINVAL, DIBELLA_EBASE, DIBELLA_ENOMEM, DIBELLA_ECUDA, DIBELLA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+RES_SEED_MISMATCH, RES_INVALID_SEED, RES_BEST_OF_PAIR, RES_BAND_OVERFLOW = 1, 2, 4, 8
+XDROP_INF = 1 << 30
+MAX_BUCKETS = 8
+
+_ERRORS = {DIBELLA_EINVAL: "invalid argument", DIBELLA_EBASE: "non-ACGT base",
+           DIBELLA_ENOMEM: "workspace too small", DIBELLA_ECUDA: "CUDA error",
+           DIBELLA_ETIMEOUT: "device wait timed out"}
+
+
+class DibellaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = "%s failed: %s (%d)" % (where, _ERRORS.get(code, "error"), code)
+        if code == DIBELLA_ECUDA:
+            msg += ": " + _lib().dibella_last_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("gap", ctypes.c_int32), ("xdrop", ctypes.c_int32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("narrow_max_xdrop", ctypes.c_int32), ("narrow_max_len", ctypes.c_int32),
+                ("narrow_band_cap", ctypes.c_int32), ("wide_blocks_per_sm", ctypes.c_int32),
+                ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
+                ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS)]
+
+    def as_dict(self) -> dict:
+        return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
+                "narrow_band_cap": self.narrow_band_cap, "wide_blocks_per_sm": self.wide_blocks_per_sm,
+                "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
+                "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)]}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Schedule":
+        s = cls()
+        for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_blocks_per_sm",
+                    "narrow_blocks_per_sm", "n_buckets"):
+            setattr(s, key, int(d[key]))
+        bounds = list(d.get("bucket_bounds", []))
+        for b in range(MAX_BUCKETS):
+            s.bucket_bounds[b] = int(bounds[b]) if b < len(bounds) else 0
+        return s
+
+
+_LIB = None
+
+
+def _lib():
+    """Load libdibella.so (compiling it first if its sources are newer)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale(path, _build.SOURCES + _build.HEADERS):
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, p64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "dibella_packed_words": ([vp, i64, p64], i32),
+            "dibella_pack_reads": ([vp, vp, i64, vp, vp, vp, p64, i32], i32),
+            "dibella_get_default_schedule": ([ctypes.POINTER(Schedule)], i32),
+            "dibella_set_default_schedule": ([ctypes.POINTER(Schedule)], i32),
+            "dibella_xdrop_workspace_bytes": ([i64, i32, p64], i32),
+            "dibella_staging_bytes": ([i64, p64], i32),
+            "dibella_xdrop_batch": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, i64, vp,
+                                     ctypes.POINTER(Schedule)], i32),
+            "dibella_xdrop_batch_host": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, vp, i64, vp,
+                                          ctypes.POINTER(Schedule)], i32),
+            "dibella_xdrop_per_pair": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, i64, vp], i32),
+            "dibella_enable_phase_timing": ([ctypes.c_int], i32),
+            "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
+            "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
+            "dibella_last_error": ([], ctypes.c_char_p),
+            "dibella_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = lib
+    return _LIB
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def exported_symbols() -> list[str]:
+    """Names the binding resolves in the loaded library."""
+    lib = _lib()
+    return [n for n in dir(lib) if n.startswith("dibella_")]
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != DIBELLA_OK:
+        raise DibellaError(rc, where)
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C ABI, one Python function per entry point -----------------------------
+
+def dibella_packed_words(ascii_offsets: np.ndarray) -> int:
+    offs = np.ascontiguousarray(ascii_offsets, dtype=np.int64)
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_packed_words(offs.ctypes.data, len(offs) - 1, ctypes.byref(out)),
+           "dibella_packed_words")
+    return out.value
+
+
+def dibella_pack_reads(ascii: np.ndarray, ascii_offsets: np.ndarray, n_threads: int = 0):
+    """Pack ASCII reads; returns (packed_words uint32, read_word_offsets int64, read_lengths int32)."""
+    ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+    offs = np.ascontiguousarray(ascii_offsets, dtype=np.int64)
+    n = len(offs) - 1
+    words = np.empty(dibella_packed_words(offs), dtype=np.uint32)
+    woffs = np.empty(n, dtype=np.int64)
+    lens = np.empty(n, dtype=np.int32)
+    bad = ctypes.c_int64(-1)
+    rc = _lib().dibella_pack_reads(ascii.ctypes.data, offs.ctypes.data, n, words.ctypes.data,
+                                   woffs.ctypes.data, lens.ctypes.data, ctypes.byref(bad), n_threads)
+    if rc == DIBELLA_EBASE:
+        raise DibellaError(rc, "dibella_pack_reads (byte %d)" % bad.value)
+    _check(rc, "dibella_pack_reads")
+    return words, woffs, lens
+
+
+def dibella_get_default_schedule() -> Schedule:
+    s = Schedule()
+    _check(_lib().dibella_get_default_schedule(ctypes.byref(s)), "dibella_get_default_schedule")
+    return s
+
+
+def dibella_set_default_schedule(s: Schedule) -> None:
+    _check(_lib().dibella_set_default_schedule(ctypes.byref(s)), "dibella_set_default_schedule")
+
+
+def dibella_xdrop_workspace_bytes(n_pairs: int, max_read_len: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_xdrop_workspace_bytes(n_pairs, max_read_len, ctypes.byref(out)),
+           "dibella_xdrop_workspace_bytes")
+    return out.value
+
+
+def dibella_staging_bytes(n_pairs: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_staging_bytes(n_pairs, ctypes.byref(out)), "dibella_staging_bytes")
+    return out.value
+
+
+def dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs, n_pairs: int,
+                        k: int, scoring: Scoring, results, workspace, workspace_bytes: int,
+                        stream=None, sched: Schedule | None = None) -> None:
+    rc = _lib().dibella_xdrop_batch(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths),
+                                    n_reads, _ptr(pairs), n_pairs, k, scoring, _ptr(results),
+                                    _ptr(workspace), workspace_bytes, _stream_handle(stream),
+                                    ctypes.byref(sched) if sched is not None else None)
+    _check(rc, "dibella_xdrop_batch")
+
+
+def dibella_xdrop_batch_host(packed_words, read_word_offsets, read_lengths, n_reads: int, host_pairs,
+                             n_pairs: int, k: int, scoring: Scoring, host_results, staging, workspace,
+                             workspace_bytes: int, stream=None, sched: Schedule | None = None) -> None:
+    rc = _lib().dibella_xdrop_batch_host(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths),
+                                         n_reads, _ptr(host_pairs), n_pairs, k, scoring,
+                                         _ptr(host_results), _ptr(staging), _ptr(workspace),
+                                         workspace_bytes, _stream_handle(stream),
+                                         ctypes.byref(sched) if sched is not None else None)
+    _check(rc, "dibella_xdrop_batch_host")
+
+
+def dibella_xdrop_per_pair(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs, n_pairs: int,
+                           k: int, scoring: Scoring, results, workspace, workspace_bytes: int,
+                           stream=None) -> None:
+    rc = _lib().dibella_xdrop_per_pair(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths),
+                                       n_reads, _ptr(pairs), n_pairs, k, scoring, _ptr(results),
+                                       _ptr(workspace), workspace_bytes, _stream_handle(stream))
+    _check(rc, "dibella_xdrop_per_pair")
+
+
+def dibella_enable_phase_timing(enable: bool) -> None:
+    _check(_lib().dibella_enable_phase_timing(1 if enable else 0), "dibella_enable_phase_timing")
+
+
+def dibella_phase_times(n_max: int = 8) -> list[float]:
+    buf = (ctypes.c_float * n_max)()
+    n = _lib().dibella_phase_times(buf, n_max)
+    if n < 0:
+        _check(n, "dibella_phase_times")
+    return [float(buf[i]) for i in range(n)]
+
+
+def dibella_batch_counters(workspace, stream=None) -> dict:
+    buf = (ctypes.c_int64 * 9)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 9)
+    if n < 0:
+        _check(n, "dibella_batch_counters")
+    keys = ["narrow", "wide", "escalated_narrow_to_wide", "escalated_wide_to_global", "band_overflow",
+            "cells_narrow", "cells_wide", "cells_wide_escalated", "cells_global"]
+    return {keys[i]: int(buf[i]) for i in range(n)}
+
+
+def dibella_last_error() -> str:
+    return _lib().dibella_last_error().decode()
+
+
+def dibella_version() -> str:
+    return _lib().dibella_version().decode()
+
+
+from .store import ReadStore, Aligner  # noqa: E402  (device-memory plumbing)
+
+__all__ = [n for n in dir() if n.startswith("dibella_")] + [
+    "PAIR_DTYPE", "RESULT_DTYPE", "Scoring", "Schedule", "DibellaError", "ReadStore", "Aligner"]

@@ -1,0 +1,1061 @@
+// X-drop seed-and-extend on GB300 (sm_103a): kernels and the C ABI.
+//
+// Computes, per candidate seed, the alignment of diBELLA Sec. 2 (pairwise
+// alignment, linear-gap scoring, X-drop search after Zhang et al. 2000) from
+// a shared k-mer seed (Sec. 2 Fig. 1, Sec. 8 seed selection), which is the
+// per-pair work of the alignment stage (Sec. 9).  The exact reading of the
+// X-drop rule (band from the live cells of the previous antidiagonal, live
+// iff H >= best - X, strict improvement, smallest i on ties, evaluated-cell
+// count) is documented on dibella_xdrop_batch in include/dibella.h.
+//
+// Pipeline of one batch (all on the caller's stream, no host sync):
+//   expand   one thread per seed: validate, seed score, two extension items
+//            (left, right) with the copy/offset of both sequences; count
+//            items per (kernel class, length bucket)
+//   scan     bucket offsets, longest bucket first (work queues are ordered
+//            so long extensions start early: Sec. 9 load imbalance from
+//            read length and X-drop early exit)
+//   scatter  item ids into the narrow and wide queues
+//   extend   persistent kernel; every warp first takes wide items (one warp
+//            per extension, band in shared memory in chunks of 32 cells),
+//            then narrow items (one lane per extension, band in per-lane
+//            shared memory); a band that outgrows its storage is re-queued
+//            for the next wider form
+//   extend   again for narrow->wide escalations
+//   global   one warp per extension with the band in workspace memory
+//   combine  seed + left + right, coordinates, cells; best seed per pair
+//
+// Arithmetic is int32 (limits on scores and read lengths in dibella.h keep
+// every value inside (-2^31, 2^31)); no tensor cores: this is not a dense
+// contraction.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dibella.h"
+
+namespace {
+
+constexpr int kNeg = -(1 << 30) - (1 << 29);  // dead / outside band; below any threshold
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kBlockThreads = kWarpsPerBlock * 32;
+constexpr int kGlobalWarps = 64;  // warps of the global-band kernel (and its band slots)
+
+// One extension of one seed: a[x] = base (a0 + x) of the packed store
+// (ascending), b[y] = base (b0 - y) (descending); a is always read in the
+// opposite complement sense of b (see expand), so a match is a 2-bit XOR of 3.
+struct Item {
+  long long a0, b0;
+  int m, n;
+  int tag;  // class << 8 | bucket, or -1 for no item
+  int pad;
+};
+static_assert(sizeof(Item) == 32, "item is 32 bytes");
+
+struct ExtOut {
+  int best, i_end, j_end, status;
+  long long cells;
+};
+static_assert(sizeof(ExtOut) == 24, "ext out is 24 bytes");
+
+struct Counters {
+  unsigned int tail[4];   // queue sizes: 0 narrow, 1 wide, 2 narrow->wide, 3 wide->global
+  unsigned int head[4];   // pop cursors
+  unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
+  unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
+  unsigned int stat[8];   // 0 narrow routed, 1 wide routed, 2 esc1, 3 esc2, 4 overflow
+  unsigned long long cells[4];  // cells of finished extensions: narrow, wide pass 1, wide pass 2, global
+};
+
+enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQEsc2 = 3 };
+
+struct Workspace {
+  Counters* counters;
+  Item* items;
+  ExtOut* ext;
+  int* queue[4];
+  int* gband;
+  int gcap;
+};
+
+struct Scoring {
+  int M, S, G, X;
+};
+
+struct ExtendParams {
+  const uint32_t* __restrict__ words;
+  const Item* __restrict__ items;
+  ExtOut* ext;
+  Counters* cnt;
+  const int* wide_q;
+  int wide_q_id;     // which head/tail pair belongs to wide_q
+  const int* narrow_q;
+  int narrow_q_id;   // -1: no narrow phase
+  int* esc_q;        // wide overflow goes here (global kernel) ...
+  int esc_q_id;
+  int* esc_narrow_q; // narrow overflow goes here (second extend launch)
+  int esc_narrow_q_id;
+  Scoring sc;
+  int* gband;
+  int gcap;
+  int wide_cells_slot;  // Counters::cells index credited by this launch's wide phase
+};
+
+__device__ __forceinline__ uint32_t base_window(const uint32_t* __restrict__ words, long long idx) {
+  // 16 bases starting at base index idx (>= 0), base t at bits 2t.
+  const long long w = idx >> 4;
+  const uint32_t lo = __ldg(words + w), hi = __ldg(words + w + 1);
+  return __funnelshift_r(lo, hi, (unsigned)(idx & 15) * 2u);
+}
+
+__device__ __forceinline__ int base_at(const uint32_t* __restrict__ words, long long idx) {
+  return (int)((__ldg(words + (idx >> 4)) >> ((unsigned)(idx & 15) * 2u)) & 3u);
+}
+
+__device__ __forceinline__ unsigned pop_warp(Counters* cnt, int q) {
+  unsigned idx = 0;
+  if ((threadIdx.x & 31) == 0) idx = atomicAdd(&cnt->head[q], 1u);
+  return __shfl_sync(kFull, idx, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Wide form: one warp per extension.  Three antidiagonals in a circular array
+// of `cap` (power of two) cells; lane l computes cell i = i0 + l of each chunk
+// of 32 cells.  Returns false if the band outgrew cap - 3 cells.
+template <bool kGlobalBand>
+__device__ bool extend_warp(const uint32_t* __restrict__ words, const Item& it, const Scoring sc,
+                            int* arr, int cap, ExtOut* out) {
+  const int lane = threadIdx.x & 31;
+  const int mask = cap - 1;
+  int* H2 = arr;            // antidiagonal d-2
+  int* H1 = arr + cap;      // d-1
+  int* H0 = arr + 2 * cap;  // d
+  const int m = it.m, n = it.n;
+  // d = 0: cell (0,0) = 0 with guards; d = -1: no cell (guards read as dead).
+  if (lane == 0) {
+    H1[0] = 0;
+    H1[mask] = kNeg;      // i = -1
+    H1[1 & mask] = kNeg;  // i = 1
+    H2[mask] = kNeg;
+    H2[0] = kNeg;
+  }
+  __syncwarp();
+  int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  long long cells = 0;
+  for (int d = 1; d <= m + n; ++d) {
+    const int lo = max(live_lo, d - n);
+    const int hi = min(min(live_hi + 1, d), m);
+    if (hi - lo + 3 > cap) return false;
+    const int thr = best - sc.X;
+    const long long abase = it.a0 - 1, bbase = it.b0 + 1 - d;
+    int vmax = kNeg, first = INT32_MAX, last = -1;
+    for (int i0 = lo; i0 <= hi; i0 += 32) {
+      const int i = i0 + lane;
+      int h = kNeg;
+      if (i <= hi) {
+        const int lf = H1[i & mask];
+        const int u = H1[(i - 1) & mask];
+        const int dg = H2[(i - 1) & mask];
+        const int ca = base_at(words, abase + i), cb = base_at(words, bbase + i);
+        const int sub = (ca ^ cb) == 3 ? sc.M : sc.S;
+        h = max(max(u, lf) + sc.G, dg + sub);
+        h = h >= thr ? h : kNeg;
+        H0[i & mask] = h;
+      }
+      vmax = max(vmax, h);
+      const unsigned bl = __ballot_sync(kFull, h != kNeg);
+      if (bl) {
+        if (first == INT32_MAX) first = i0 + __ffs(bl) - 1;
+        last = i0 + 31 - __clz(bl);
+      }
+    }
+    cells += hi - lo + 1;
+    if (lane == 0) H0[(lo - 1) & mask] = kNeg;
+    if (lane == 1) H0[(hi + 1) & mask] = kNeg;
+    vmax = __reduce_max_sync(kFull, vmax);
+    __syncwarp();
+    if (vmax == kNeg) break;
+    if (vmax > best) {
+      for (int i0 = first;; i0 += 32) {
+        const int i = i0 + lane;
+        const unsigned bl = __ballot_sync(kFull, i <= last && H0[i & mask] == vmax);
+        if (bl) {
+          bi = i0 + __ffs(bl) - 1;
+          break;
+        }
+      }
+      best = vmax;
+      bj = d - bi;
+    }
+    live_lo = first;
+    live_hi = last;
+    int* t = H2;
+    H2 = H1;
+    H1 = H0;
+    H0 = t;
+  }
+  if (lane == 0) {
+    out->best = best;
+    out->i_end = bi;
+    out->j_end = bj;
+    out->status = 0;
+    out->cells = cells;
+  }
+  __syncwarp();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Narrow form: one lane per extension.  Two antidiagonal arrays of WT cells
+// per lane, lane-interleaved in shared memory (cell slot s of array A of a
+// lane at word ((A*WT + s) * 32 + lane), so the 32 lanes never conflict).
+// Slot s holds cell i = f + s; the frame f moves up when the band reaches the
+// top.  The band is walked cell by cell; the array of d-2 is overwritten in
+// place with d (its value is read one cell ahead).
+template <int WT>
+struct NarrowLane {
+  long long a0, b0;
+  int m, n, item;
+  int d, live_lo, live_hi, best, bi, bj, f, h1;
+  long long cells;
+};
+
+template <int WT>
+__device__ __forceinline__ int& nslot(int* wbase, int A, int s, int lane) {
+  return wbase[((A * WT + s) << 5) + lane];
+}
+
+template <int WT>
+__device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, int* wbase, int lane) {
+  L.a0 = it.a0;
+  L.b0 = it.b0;
+  L.m = it.m;
+  L.n = it.n;
+  L.item = item;
+  L.d = 1;
+  L.live_lo = 0;
+  L.live_hi = 0;
+  L.best = 0;
+  L.bi = 0;
+  L.bj = 0;
+  L.f = -1;
+  L.h1 = 0;
+  L.cells = 0;
+  nslot<WT>(wbase, 0, 0, lane) = kNeg;  // d = 0: i = -1
+  nslot<WT>(wbase, 0, 1, lane) = 0;     //        i = 0
+  nslot<WT>(wbase, 0, 2, lane) = kNeg;  //        i = 1
+  nslot<WT>(wbase, 1, 0, lane) = kNeg;  // d = -1: i = -1
+  nslot<WT>(wbase, 1, 1, lane) = kNeg;  //         i = 0
+}
+
+// One antidiagonal for one lane.  Returns 1 when the extension finished,
+// 2 when its band outgrew the lane's storage, 0 otherwise.
+template <int WT>
+__device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words, const Scoring sc,
+                           int* wbase, int lane) {
+  const int d = L.d;
+  const int lo = max(L.live_lo, d - L.n);
+  const int hi = min(min(L.live_hi + 1, d), L.m);
+  const int h1 = L.h1, h2 = 1 - h1;
+  if (hi + 1 - L.f >= WT) {
+    if (hi - lo + 3 > WT) return 2;
+    const int nf = lo - 1;
+    for (int i = lo - 1; i <= hi; ++i) nslot<WT>(wbase, h1, i - nf, lane) = nslot<WT>(wbase, h1, i - L.f, lane);
+    for (int i = lo - 1; i <= hi - 1; ++i) nslot<WT>(wbase, h2, i - nf, lane) = nslot<WT>(wbase, h2, i - L.f, lane);
+    L.f = nf;
+  }
+  const int f = L.f;
+  const int thr = L.best - sc.X;
+  int u = nslot<WT>(wbase, h1, lo - 1 - f, lane);
+  int dg = nslot<WT>(wbase, h2, lo - 1 - f, lane);
+  int vmax = kNeg;
+  const long long abase = L.a0 - 1, bbase = L.b0 + 1 - d;
+  for (int i = lo; i <= hi; i += 16) {
+    const uint32_t wa = base_window(words, abase + i);
+    const uint32_t wb = base_window(words, bbase + i);
+    const uint32_t x = ~(wa ^ wb);
+    const uint32_t mm = (x | (x >> 1)) & 0x55555555u;
+    const int cnt = min(16, hi - i + 1);
+    int* p1 = &nslot<WT>(wbase, h1, i - f, lane);
+    int* p2 = &nslot<WT>(wbase, h2, i - f, lane);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < cnt) {
+        const int lf = p1[t * 32];
+        const int dn = p2[t * 32];
+        const int sub = ((mm >> (2 * t)) & 1u) ? sc.S : sc.M;
+        int h = max(max(u, lf) + sc.G, dg + sub);
+        h = h >= thr ? h : kNeg;
+        p2[t * 32] = h;
+        vmax = max(vmax, h);
+        u = lf;
+        dg = dn;
+      }
+    }
+  }
+  nslot<WT>(wbase, h2, lo - 1 - f, lane) = kNeg;
+  nslot<WT>(wbase, h2, hi + 1 - f, lane) = kNeg;
+  L.cells += hi - lo + 1;
+  L.h1 = h2;
+  if (vmax == kNeg) return 1;
+  int llo = lo;
+  while (nslot<WT>(wbase, h2, llo - f, lane) == kNeg) ++llo;
+  int lhi = hi;
+  while (nslot<WT>(wbase, h2, lhi - f, lane) == kNeg) --lhi;
+  if (vmax > L.best) {
+    int b = llo;
+    while (nslot<WT>(wbase, h2, b - f, lane) != vmax) ++b;
+    L.best = vmax;
+    L.bi = b;
+    L.bj = d - b;
+  }
+  L.live_lo = llo;
+  L.live_hi = lhi;
+  if (d == L.m + L.n) return 1;
+  L.d = d + 1;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent extension kernel.  Each warp owns 2*WT*32 ints of shared memory,
+// used either as 32 narrow lanes or as one wide band of the largest power of
+// two not above a third of it.
+template <int WT>
+__global__ void __launch_bounds__(kBlockThreads) extend_kernel(ExtendParams p) {
+  extern __shared__ int smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int* wbase = smem + warp * (2 * WT * 32);
+  constexpr int kWideCap = (2 * WT * 32 / 3) >= 1024 ? 1024 : ((2 * WT * 32 / 3) >= 512 ? 512 : 256);
+
+  // Phase 1: wide items, one warp each, longest first.
+  if (p.wide_q != nullptr) {
+    const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+    for (;;) {
+      const unsigned q = pop_warp(p.cnt, p.wide_q_id);
+      if (q >= tail) break;
+      const int item = p.wide_q[q];
+      const Item it = p.items[item];
+      if (!extend_warp<false>(p.words, it, p.sc, wbase, kWideCap, p.ext + item)) {
+        if (lane == 0) {
+          const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+          p.esc_q[s] = item;
+          atomicAdd(&p.cnt->stat[3], 1u);
+        }
+      } else if (lane == 0) {
+        atomicAdd(&p.cnt->cells[p.wide_cells_slot], (unsigned long long)p.ext[item].cells);
+      }
+      __syncwarp();
+    }
+  }
+  if (p.narrow_q == nullptr) return;
+
+  // Phase 2: narrow items, one lane each; lanes refill independently.
+  const unsigned ntail = *((volatile unsigned*)&p.cnt->tail[p.narrow_q_id]);
+  NarrowLane<WT> L;
+  bool active = false, exhausted = false;
+  for (;;) {
+    const unsigned want = __ballot_sync(kFull, !active && !exhausted);
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&p.cnt->head[p.narrow_q_id], (unsigned)__popc(want));
+      base = __shfl_sync(kFull, base, leader);
+      if (want & (1u << lane)) {
+        const unsigned q = base + __popc(want & ((1u << lane) - 1u));
+        if (q < ntail) {
+          const int item = p.narrow_q[q];
+          const Item it = p.items[item];
+          narrow_init<WT>(L, it, item, wbase, lane);
+          active = true;
+          if (it.m + it.n == 0) {
+            ExtOut o;
+            o.best = 0; o.i_end = 0; o.j_end = 0; o.status = 0; o.cells = 0;
+            p.ext[item] = o;
+            active = false;
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) {
+      if (__all_sync(kFull, exhausted)) break;
+      continue;
+    }
+    if (active) {
+      const int r = narrow_step<WT>(L, p.words, p.sc, wbase, lane);
+      if (r == 1) {
+        ExtOut o;
+        o.best = L.best; o.i_end = L.bi; o.j_end = L.bj; o.status = 0; o.cells = L.cells;
+        p.ext[L.item] = o;
+        atomicAdd(&p.cnt->cells[0], (unsigned long long)L.cells);
+        active = false;
+      } else if (r == 2) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_narrow_q_id], 1u);
+        p.esc_narrow_q[s] = L.item;
+        atomicAdd(&p.cnt->stat[2], 1u);
+        active = false;
+      }
+    }
+  }
+}
+
+// Global-band form: one warp per extension, band in workspace memory.
+__global__ void __launch_bounds__(kBlockThreads) global_kernel(ExtendParams p) {
+  const int gwarp = (blockIdx.x * kBlockThreads + threadIdx.x) >> 5;
+  int* arr = p.gband + (size_t)gwarp * 3 * p.gcap;
+  const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  for (;;) {
+    const unsigned q = pop_warp(p.cnt, p.wide_q_id);
+    if (q >= tail) break;
+    const int item = p.wide_q[q];
+    const Item it = p.items[item];
+    if (!extend_warp<true>(p.words, it, p.sc, arr, p.gcap, p.ext + item)) {
+      if ((threadIdx.x & 31) == 0) {
+        ExtOut o;
+        o.best = 0; o.i_end = 0; o.j_end = 0; o.status = DIBELLA_RES_BAND_OVERFLOW; o.cells = 0;
+        p.ext[item] = o;
+        atomicAdd(&p.cnt->stat[4], 1u);
+      }
+    } else if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&p.cnt->cells[3], (unsigned long long)p.ext[item].cells);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct ExpandParams {
+  const uint32_t* __restrict__ words;
+  const long long* __restrict__ read_word_offsets;
+  const int* __restrict__ read_lengths;
+  long long n_reads;
+  const dibella_pair_t* __restrict__ pairs;
+  long long n_pairs;
+  int k;
+  Scoring sc;
+  dibella_result_t* results;
+  Item* items;
+  Counters* cnt;
+  int narrow_max_x, narrow_max_len, n_buckets;
+  int bounds[DIBELLA_MAX_BUCKETS];
+};
+
+__device__ __forceinline__ unsigned long long bases64(const uint32_t* __restrict__ words, long long idx) {
+  const long long w = idx >> 4;
+  const unsigned sh = (unsigned)(idx & 15) * 2u;
+  const uint32_t w0 = __ldg(words + w), w1 = __ldg(words + w + 1), w2 = __ldg(words + w + 2);
+  return (unsigned long long)__funnelshift_r(w0, w1, sh) |
+         ((unsigned long long)__funnelshift_r(w1, w2, sh) << 32);
+}
+
+__device__ __forceinline__ long long copy_words(long long len) { return ((len + 15) / 16 + 3) / 4 * 4; }
+
+__global__ void expand_kernel(ExpandParams p) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.n_pairs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const dibella_pair_t pr = p.pairs[t];
+    dibella_result_t r;
+    memset(&r, 0, sizeof(r));
+    Item L, R;
+    L.a0 = L.b0 = R.a0 = R.b0 = 0;
+    L.m = L.n = R.m = R.n = 0;
+    L.tag = R.tag = -1;
+    L.pad = R.pad = 0;
+    const int k = p.k;
+    bool valid = (long long)pr.read_a < p.n_reads && (long long)pr.read_b < p.n_reads && pr.strand <= 1;
+    long long lenA = 0, lenB = 0;
+    if (valid) {
+      lenA = p.read_lengths[pr.read_a];
+      lenB = p.read_lengths[pr.read_b];
+      valid = (long long)pr.pos_a + k <= lenA && (long long)pr.pos_b + k <= lenB;
+    }
+    if (!valid) {
+      r.status = DIBELLA_RES_INVALID_SEED;
+    } else {
+      const long long offA = p.read_word_offsets[pr.read_a], offB = p.read_word_offsets[pr.read_b];
+      const long long fA = offA * 16, rA = (offA + copy_words(lenA)) * 16;
+      const long long fB = offB * 16, rB = (offB + copy_words(lenB)) * 16;
+      const long long pa = pr.pos_a;
+      const long long pb = pr.strand ? lenB - pr.pos_b - k : (long long)pr.pos_b;  // in B'
+      // Seed score: A[pa, pa+k) against B'[pb, pb+k), B' = F_B or R_B.
+      const unsigned long long sa = bases64(p.words, fA + pa);
+      const unsigned long long sb = bases64(p.words, (pr.strand ? rB : fB) + pb);
+      const unsigned long long x = sa ^ sb;
+      const unsigned long long kmask = k == 32 ? ~0ull : ((1ull << (2 * k)) - 1ull);
+      const int mism = __popcll((x | (x >> 1)) & 0x5555555555555555ull & kmask);
+      r.score = k * p.sc.M + mism * (p.sc.S - p.sc.M);
+      r.status = mism ? DIBELLA_RES_SEED_MISMATCH : 0;
+      // Left: a[x] = A[pa-1-x] = comp(R_A[lenA-pa+x]); b[y] = B'[pb-1-y].
+      L.a0 = rA + (lenA - pa);
+      L.m = (int)pa;
+      L.b0 = (pr.strand ? rB : fB) + (pb - 1);
+      L.n = (int)pb;
+      // Right: a[x] = A[pa+k+x]; b[y] = B'[pb+k+y] = comp(copy'[lenB-1-pb-k-y]).
+      R.a0 = fA + pa + k;
+      R.m = (int)(lenA - pa - k);
+      R.b0 = (pr.strand ? fB : rB) + (lenB - 1 - pb - k);
+      R.n = (int)(lenB - pb - k);
+      Item* both[2] = {&L, &R};
+      for (int s = 0; s < 2; ++s) {
+        Item* it = both[s];
+        const int key = min(it->m, it->n);
+        const int cls = (p.sc.X <= p.narrow_max_x && key <= p.narrow_max_len) ? 0 : 1;
+        int b = 0;
+        while (b < p.n_buckets - 1 && key >= p.bounds[b]) ++b;
+        it->tag = (cls << 8) | b;
+        atomicAdd(&p.cnt->bucket_count[cls][b], 1u);
+      }
+    }
+    p.results[t] = r;
+    p.items[2 * t] = L;
+    p.items[2 * t + 1] = R;
+  }
+}
+
+__global__ void scan_kernel(Counters* cnt, int n_buckets) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int c = 0; c < 2; ++c) {
+    unsigned pos = 0;
+    for (int b = n_buckets - 1; b >= 0; --b) {
+      cnt->bucket_cursor[c][b] = pos;
+      pos += cnt->bucket_count[c][b];
+    }
+    cnt->tail[c == 0 ? kQNarrow : kQWide] = pos;
+    cnt->stat[c] = pos;
+  }
+}
+
+__global__ void scatter_kernel(const Item* __restrict__ items, long long n_items, Counters* cnt,
+                               int* narrow_q, int* wide_q) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_items;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int tag = items[t].tag;
+    if (tag < 0) continue;
+    const int cls = tag >> 8, b = tag & 255;
+    const unsigned s = atomicAdd(&cnt->bucket_cursor[cls][b], 1u);
+    (cls == 0 ? narrow_q : wide_q)[s] = (int)t;
+  }
+}
+
+struct CombineParams {
+  const int* __restrict__ read_lengths;
+  const dibella_pair_t* __restrict__ pairs;
+  long long n_pairs;
+  int k;
+  const ExtOut* __restrict__ ext;
+  dibella_result_t* results;
+};
+
+__global__ void combine_kernel(CombineParams p) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.n_pairs;
+       t += (long long)gridDim.x * blockDim.x) {
+    dibella_result_t r = p.results[t];
+    if (r.status & DIBELLA_RES_INVALID_SEED) continue;
+    const ExtOut L = p.ext[2 * t], R = p.ext[2 * t + 1];
+    if ((L.status | R.status) & DIBELLA_RES_BAND_OVERFLOW) {
+      const int st = r.status;
+      memset(&r, 0, sizeof(r));
+      r.status = st | DIBELLA_RES_BAND_OVERFLOW;
+      p.results[t] = r;
+      continue;
+    }
+    const dibella_pair_t pr = p.pairs[t];
+    const long long lenB = p.read_lengths[pr.read_b];
+    const long long pa = pr.pos_a;
+    const long long pb = pr.strand ? lenB - pr.pos_b - p.k : (long long)pr.pos_b;
+    r.score += L.best + R.best;
+    r.score_left = L.best;
+    r.score_right = R.best;
+    r.begin_a = (uint32_t)(pa - L.i_end);
+    r.end_a = (uint32_t)(pa + p.k + R.i_end);
+    const long long bb = pb - L.j_end, be = pb + p.k + R.j_end;
+    if (pr.strand) {
+      r.begin_b = (uint32_t)(lenB - be);
+      r.end_b = (uint32_t)(lenB - bb);
+    } else {
+      r.begin_b = (uint32_t)bb;
+      r.end_b = (uint32_t)be;
+    }
+    r.cells = L.cells + R.cells;
+    p.results[t] = r;
+  }
+}
+
+__global__ void best_of_pair_kernel(const dibella_pair_t* __restrict__ pairs, long long n,
+                                    dibella_result_t* results) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const dibella_pair_t pr = pairs[t];
+    if (t > 0 && pairs[t - 1].read_a == pr.read_a && pairs[t - 1].read_b == pr.read_b) continue;
+    long long best = -1;
+    int best_score = 0;
+    for (long long u = t; u < n && pairs[u].read_a == pr.read_a && pairs[u].read_b == pr.read_b; ++u) {
+      const dibella_result_t& r = results[u];
+      if (r.status & (DIBELLA_RES_INVALID_SEED | DIBELLA_RES_BAND_OVERFLOW)) continue;
+      if (best < 0 || r.score > best_score) {
+        best = u;
+        best_score = r.score;
+      }
+    }
+    if (best >= 0) results[best].status |= DIBELLA_RES_BEST_OF_PAIR;
+  }
+}
+
+// One launch per seed (baseline form): one warp aligns the left then the right
+// extension of seed `t`, band in shared memory (1024 cells) or, if it
+// outgrows that, in the workspace band slot 0.
+__global__ void __launch_bounds__(32) per_pair_kernel(const uint32_t* __restrict__ words,
+                                                      const Item* __restrict__ items, ExtOut* ext,
+                                                      long long t, Scoring sc, int* gband, int gcap) {
+  __shared__ int arr[3 * 1024];
+  for (int s = 0; s < 2; ++s) {
+    const Item it = items[2 * t + s];
+    if (it.tag < 0) continue;
+    if (!extend_warp<false>(words, it, sc, arr, 1024, ext + 2 * t + s)) {
+      if (!extend_warp<true>(words, it, sc, gband, gcap, ext + 2 * t + s)) {
+        if (threadIdx.x == 0) {
+          ExtOut o;
+          o.best = 0; o.i_end = 0; o.j_end = 0; o.status = DIBELLA_RES_BAND_OVERFLOW; o.cells = 0;
+          ext[2 * t + s] = o;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+thread_local std::string g_last_error;
+
+std::mutex g_mu;
+dibella_schedule_t g_default_schedule = {
+    /*narrow_max_xdrop=*/16, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/64,
+    /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0, /*n_buckets=*/6,
+    {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
+
+struct DeviceInfo {
+  bool ready = false;
+  int sms = 0;
+  int blocks[3] = {0, 0, 0};   // extend_kernel<32/48/64> blocks per SM at full smem
+  int global_blocks = 0;
+};
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+
+bool g_timing = false;
+cudaEvent_t g_ev[8] = {};
+int g_ev_count = 0;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return DIBELLA_ECUDA;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int gband_cap_for(int32_t max_read_len) {
+  int cap = 64;
+  while (cap < max_read_len + 4 && cap < (1 << 25)) cap <<= 1;
+  return cap;
+}
+
+struct Layout {
+  size_t counters, items, ext, queue[4], gband, total;
+};
+
+Layout layout_for(long long n_pairs, int gcap) {
+  Layout L;
+  size_t off = 0;
+  L.counters = off;
+  off = align256(off + sizeof(Counters));
+  L.items = off;
+  off = align256(off + sizeof(Item) * 2 * (size_t)n_pairs);
+  L.ext = off;
+  off = align256(off + sizeof(ExtOut) * 2 * (size_t)n_pairs);
+  for (int q = 0; q < 4; ++q) {
+    L.queue[q] = off;
+    off = align256(off + sizeof(int) * 2 * (size_t)n_pairs);
+  }
+  L.gband = off;
+  off = align256(off + sizeof(int) * 3 * (size_t)gcap * kGlobalWarps);
+  L.total = off;
+  return L;
+}
+
+// Largest band capacity whose global band region fits in `bytes`.
+int gcap_from_workspace(long long n_pairs, long long bytes) {
+  int best = 0;
+  for (int cap = 64; cap <= (1 << 25); cap <<= 1)
+    if ((long long)layout_for(n_pairs, cap).total <= bytes) best = cap;
+  return best;
+}
+
+template <int WT>
+size_t extend_smem() {
+  return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(int);
+}
+
+int device_info(DeviceInfo** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return DIBELLA_EINVAL;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceInfo& D = g_dev[dev];
+  if (!D.ready) {
+    e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const void* fns[3] = {(const void*)extend_kernel<32>, (const void*)extend_kernel<48>,
+                          (const void*)extend_kernel<64>};
+    const size_t sm[3] = {extend_smem<32>(), extend_smem<48>(), extend_smem<64>()};
+    for (int v = 0; v < 3; ++v) {
+      e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[v]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.blocks[v], fns[v], kBlockThreads, sm[v]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (D.blocks[v] < 1) D.blocks[v] = 1;
+    }
+    D.ready = true;
+  }
+  *out = &D;
+  return DIBELLA_OK;
+}
+
+int validate_schedule(const dibella_schedule_t& s) {
+  if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
+  if (s.n_buckets < 1 || s.n_buckets > DIBELLA_MAX_BUCKETS) return DIBELLA_EINVAL;
+  if (s.wide_blocks_per_sm < 0 || s.narrow_blocks_per_sm < 0) return DIBELLA_EINVAL;
+  for (int b = 1; b < s.n_buckets - 1; ++b)
+    if (s.bucket_bounds[b] < s.bucket_bounds[b - 1]) return DIBELLA_EINVAL;
+  return DIBELLA_OK;
+}
+
+int validate_common(long long n_reads, long long n_pairs, int k, const dibella_scoring_t& sc) {
+  if (n_reads < 0 || n_pairs < 0 || n_pairs > (1ll << 29)) return DIBELLA_EINVAL;
+  if (k < 1 || k > DIBELLA_MAX_K) return DIBELLA_EINVAL;
+  if (sc.match <= 0 || sc.match > DIBELLA_MAX_SCORE) return DIBELLA_EINVAL;
+  if (sc.mismatch > 0 || sc.mismatch < -DIBELLA_MAX_SCORE) return DIBELLA_EINVAL;
+  if (sc.gap >= 0 || sc.gap < -DIBELLA_MAX_SCORE) return DIBELLA_EINVAL;
+  if (sc.xdrop < 0 || sc.xdrop > DIBELLA_XDROP_INF) return DIBELLA_EINVAL;
+  return DIBELLA_OK;
+}
+
+int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 65535) g = 65535;
+  return (int)g;
+}
+
+// Phase events: plain records on a live stream; under stream capture they
+// become external event-record nodes, so a replayed graph still times phases.
+void record(cudaStream_t st, int idx) {
+  if (!g_timing || g_ev[idx] == nullptr) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return;
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(g_ev[idx], st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(g_ev[idx], st);
+  g_ev_count = idx + 1;
+}
+
+template <int WT>
+cudaError_t launch_extend(int grid, cudaStream_t st, const ExtendParams& ep) {
+  extend_kernel<WT><<<grid, kBlockThreads, extend_smem<WT>(), st>>>(ep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extend_any(int wt, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (wt == 32) return launch_extend<32>(grid, st, ep);
+  if (wt == 48) return launch_extend<48>(grid, st, ep);
+  return launch_extend<64>(grid, st, ep);
+}
+
+int expand_and_queue(const uint32_t* words, const int64_t* offs, const int32_t* lens, int64_t n_reads,
+                     const dibella_pair_t* pairs, int64_t n_pairs, int32_t k, const dibella_scoring_t& s,
+                     dibella_result_t* results, char* ws, const Layout& L, const dibella_schedule_t& sch,
+                     cudaStream_t st) {
+  Counters* cnt = (Counters*)(ws + L.counters);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(Counters), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (n_pairs == 0) return DIBELLA_OK;
+  ExpandParams xp;
+  xp.words = words;
+  xp.read_word_offsets = (const long long*)offs;
+  xp.read_lengths = lens;
+  xp.n_reads = n_reads;
+  xp.pairs = pairs;
+  xp.n_pairs = n_pairs;
+  xp.k = k;
+  xp.sc = {s.match, s.mismatch, s.gap, s.xdrop};
+  xp.results = results;
+  xp.items = (Item*)(ws + L.items);
+  xp.cnt = cnt;
+  xp.narrow_max_x = sch.narrow_max_xdrop;
+  xp.narrow_max_len = sch.narrow_max_len;
+  xp.n_buckets = sch.n_buckets;
+  for (int b = 0; b < DIBELLA_MAX_BUCKETS; ++b) xp.bounds[b] = sch.bucket_bounds[b];
+  expand_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(xp);
+  scan_kernel<<<1, 32, 0, st>>>(cnt, sch.n_buckets);
+  scatter_kernel<<<grid_for(2 * n_pairs, 256), 256, 0, st>>>(
+      xp.items, 2 * n_pairs, cnt, (int*)(ws + L.queue[kQNarrow]), (int*)(ws + L.queue[kQWide]));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "expand launch");
+  return DIBELLA_OK;
+}
+
+int finish(const int32_t* lens, const dibella_pair_t* pairs, int64_t n_pairs, int32_t k,
+           dibella_result_t* results, const ExtOut* ext, cudaStream_t st) {
+  if (n_pairs == 0) return DIBELLA_OK;
+  CombineParams cp;
+  cp.read_lengths = lens;
+  cp.pairs = pairs;
+  cp.n_pairs = n_pairs;
+  cp.k = k;
+  cp.ext = ext;
+  cp.results = results;
+  combine_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(cp);
+  best_of_pair_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(pairs, n_pairs, results);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+  return DIBELLA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int dibella_get_default_schedule(dibella_schedule_t* out) {
+  if (!out) return DIBELLA_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *out = g_default_schedule;
+  return DIBELLA_OK;
+}
+
+int dibella_set_default_schedule(const dibella_schedule_t* sched) {
+  if (!sched || validate_schedule(*sched) != DIBELLA_OK) return DIBELLA_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_default_schedule = *sched;
+  return DIBELLA_OK;
+}
+
+int dibella_xdrop_workspace_bytes(int64_t n_pairs, int32_t max_read_len, int64_t* bytes_out) {
+  if (!bytes_out || n_pairs < 0 || n_pairs > (1ll << 29) || max_read_len < 0 ||
+      max_read_len > DIBELLA_MAX_READ_LEN)
+    return DIBELLA_EINVAL;
+  *bytes_out = (int64_t)layout_for(n_pairs, gband_cap_for(max_read_len)).total;
+  return DIBELLA_OK;
+}
+
+int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                        const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                        int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
+                        dibella_result_t* results, void* workspace, int64_t workspace_bytes,
+                        void* stream, const dibella_schedule_t* sched) {
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  if (n_pairs > 0 && (!packed_words || !read_word_offsets || !read_lengths || !pairs || !results))
+    return DIBELLA_EINVAL;
+  if (!workspace || ((uintptr_t)workspace & 255)) return DIBELLA_EINVAL;
+  dibella_schedule_t sch;
+  if (sched) {
+    if (validate_schedule(*sched) != DIBELLA_OK) return DIBELLA_EINVAL;
+    sch = *sched;
+  } else {
+    dibella_get_default_schedule(&sch);
+  }
+  const int gcap = gcap_from_workspace(n_pairs, workspace_bytes);
+  if (gcap < 64) return DIBELLA_ENOMEM;
+  DeviceInfo* D = nullptr;
+  rc = device_info(&D);
+  if (rc != DIBELLA_OK) return rc;
+  const Layout L = layout_for(n_pairs, gcap);
+  char* ws = (char*)workspace;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  record(st, 0);
+  rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
+                        scoring, results, ws, L, sch, st);
+  if (rc != DIBELLA_OK) return rc;
+  record(st, 1);
+  if (n_pairs == 0) return DIBELLA_OK;
+
+  ExtendParams ep;
+  ep.words = packed_words;
+  ep.items = (const Item*)(ws + L.items);
+  ep.ext = (ExtOut*)(ws + L.ext);
+  ep.cnt = (Counters*)(ws + L.counters);
+  ep.sc = {scoring.match, scoring.mismatch, scoring.gap, scoring.xdrop};
+  ep.gband = (int*)(ws + L.gband);
+  ep.gcap = gcap;
+  int* q[4];
+  for (int i = 0; i < 4; ++i) q[i] = (int*)(ws + L.queue[i]);
+  const int wt = sch.narrow_band_cap;
+  const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
+  int bps = D->blocks[vi];
+  if (sch.narrow_blocks_per_sm > 0) bps = std::min(bps, sch.narrow_blocks_per_sm);
+  const int grid = D->sms * bps;
+
+  // Pass 1: wide queue, then narrow queue; escalations to Esc1 / Esc2.
+  ep.wide_q = q[kQWide];
+  ep.wide_q_id = kQWide;
+  ep.narrow_q = q[kQNarrow];
+  ep.narrow_q_id = kQNarrow;
+  ep.esc_q = q[kQEsc2];
+  ep.esc_q_id = kQEsc2;
+  ep.esc_narrow_q = q[kQEsc1];
+  ep.esc_narrow_q_id = kQEsc1;
+  ep.wide_cells_slot = 1;
+  cudaError_t e = launch_extend_any(wt, grid, st, ep);
+  if (e != cudaSuccess) return cuda_fail(e, "extend launch");
+  record(st, 2);
+  // Pass 2: narrow->wide escalations (wide form only).
+  ep.wide_q = q[kQEsc1];
+  ep.wide_q_id = kQEsc1;
+  ep.narrow_q = nullptr;
+  ep.narrow_q_id = -1;
+  ep.wide_cells_slot = 2;
+  e = launch_extend_any(wt, grid, st, ep);
+  if (e != cudaSuccess) return cuda_fail(e, "extend launch (escalation)");
+  // Pass 3: wide->global escalations.
+  ep.wide_q = q[kQEsc2];
+  ep.wide_q_id = kQEsc2;
+  global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "global launch");
+  record(st, 3);
+  rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
+  record(st, 4);
+  return rc;
+}
+
+int dibella_staging_bytes(int64_t n_pairs, int64_t* bytes_out) {
+  if (!bytes_out || n_pairs < 0 || n_pairs > (1ll << 29)) return DIBELLA_EINVAL;
+  *bytes_out = (int64_t)(align256(sizeof(dibella_pair_t) * (size_t)n_pairs) +
+                         align256(sizeof(dibella_result_t) * (size_t)n_pairs));
+  return DIBELLA_OK;
+}
+
+int dibella_xdrop_batch_host(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                             const int32_t* read_lengths, int64_t n_reads,
+                             const dibella_pair_t* host_pairs, int64_t n_pairs, int32_t k,
+                             dibella_scoring_t scoring, dibella_result_t* host_results, void* staging,
+                             void* workspace, int64_t workspace_bytes, void* stream,
+                             const dibella_schedule_t* sched) {
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  if (n_pairs > 0 && (!host_pairs || !host_results || !staging)) return DIBELLA_EINVAL;
+  if (staging && ((uintptr_t)staging & 255)) return DIBELLA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  dibella_pair_t* dpairs = (dibella_pair_t*)staging;
+  dibella_result_t* dres = (dibella_result_t*)((char*)staging + align256(sizeof(dibella_pair_t) * (size_t)n_pairs));
+  if (n_pairs > 0) {
+    cudaError_t e = cudaMemcpyAsync(dpairs, host_pairs, sizeof(dibella_pair_t) * n_pairs,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+  }
+  rc = dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads, dpairs, n_pairs, k,
+                           scoring, dres, workspace, workspace_bytes, stream, sched);
+  if (rc != DIBELLA_OK) return rc;
+  if (n_pairs > 0) {
+    cudaError_t e = cudaMemcpyAsync(host_results, dres, sizeof(dibella_result_t) * n_pairs,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return DIBELLA_OK;
+}
+
+int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                           const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                           int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
+                           dibella_result_t* results, void* workspace, int64_t workspace_bytes,
+                           void* stream) {
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  if (n_pairs > 0 && (!packed_words || !read_word_offsets || !read_lengths || !pairs || !results))
+    return DIBELLA_EINVAL;
+  if (!workspace || ((uintptr_t)workspace & 255)) return DIBELLA_EINVAL;
+  const int gcap = gcap_from_workspace(n_pairs, workspace_bytes);
+  if (gcap < 64) return DIBELLA_ENOMEM;
+  const Layout L = layout_for(n_pairs, gcap);
+  char* ws = (char*)workspace;
+  cudaStream_t st = (cudaStream_t)stream;
+  dibella_schedule_t sch;
+  dibella_get_default_schedule(&sch);
+  rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
+                        scoring, results, ws, L, sch, st);
+  if (rc != DIBELLA_OK) return rc;
+  const Scoring sc = {scoring.match, scoring.mismatch, scoring.gap, scoring.xdrop};
+  for (long long t = 0; t < n_pairs; ++t) {
+    per_pair_kernel<<<1, 32, 0, st>>>(packed_words, (const Item*)(ws + L.items), (ExtOut*)(ws + L.ext), t,
+                                      sc, (int*)(ws + L.gband), gcap);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "per-pair launch");
+  return finish(read_lengths, pairs, n_pairs, k, results, (const ExtOut*)(ws + L.ext), st);
+}
+
+int dibella_enable_phase_timing(int enable) {
+  if (enable) {
+    for (int i = 0; i < 8; ++i) {
+      if (g_ev[i] != nullptr) continue;
+      cudaError_t e = cudaEventCreate(&g_ev[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  g_timing = enable != 0;
+  g_ev_count = 0;
+  return DIBELLA_OK;
+}
+
+int dibella_phase_times(float* ms_out, int n_max) {
+  if (!ms_out || n_max < 0) return DIBELLA_EINVAL;
+  if (g_ev_count < 2) return 0;
+  cudaError_t e = cudaEventSynchronize(g_ev[g_ev_count - 1]);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+  int n = 0;
+  for (int i = 0; i + 1 < g_ev_count && n < n_max; ++i) {
+    float ms = 0;
+    e = cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ms_out[n++] = ms;
+  }
+  return n;
+}
+
+int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max) {
+  if (!workspace || !out || n_max < 0) return DIBELLA_EINVAL;
+  Counters c;
+  cudaError_t e = cudaMemcpyAsync(&c, workspace, sizeof(c), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  const int64_t v[9] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4],
+                        (int64_t)c.cells[0], (int64_t)c.cells[1], (int64_t)c.cells[2],
+                        (int64_t)c.cells[3]};
+  int n = std::min(n_max, 9);
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
+}
+
+const char* dibella_last_error(void) { return g_last_error.c_str(); }
+
+const char* dibella_version(void) { return "dibella-gb300 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+"""Device-memory plumbing around the C ABI: a resident packed read store and an
+aligner that owns its workspace.  No alignment arithmetic happens here."""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the dibella X-drop path needs a CUDA GPU; none is visible")
+    return torch
+
+
+class ReadStore:
+    """Reads packed by dibella_pack_reads and resident in HBM (diBELLA Sec. 3's
+    2-bit encoding, both orientations; layout in include/dibella.h)."""
+
+    def __init__(self, words: np.ndarray, word_offsets: np.ndarray, lengths: np.ndarray, device="cuda"):
+        torch = _torch()
+        self.n_reads = int(len(lengths))
+        self.max_len = int(lengths.max()) if len(lengths) else 0
+        self.n_bases = int(lengths.sum()) if len(lengths) else 0
+        self.words = torch.from_numpy(words.view(np.int32)).to(device)
+        self.word_offsets = torch.from_numpy(np.ascontiguousarray(word_offsets)).to(device)
+        self.lengths = torch.from_numpy(np.ascontiguousarray(lengths)).to(device)
+        self.lengths_host = np.ascontiguousarray(lengths)
+
+    @classmethod
+    def from_ascii(cls, ascii: np.ndarray, offsets: np.ndarray, device="cuda", n_threads: int = 0):
+        from . import dibella_pack_reads
+        words, woffs, lens = dibella_pack_reads(ascii, offsets, n_threads)
+        return cls(words, woffs, lens, device)
+
+    @property
+    def nbytes(self) -> int:
+        return self.words.numel() * 4 + self.word_offsets.numel() * 8 + self.lengths.numel() * 4
+
+
+class Aligner:
+    """Runs dibella_xdrop_batch on a ReadStore with a reusable workspace."""
+
+    def __init__(self, store: ReadStore, max_pairs: int, k: int = 17, device="cuda"):
+        from . import dibella_xdrop_workspace_bytes
+        torch = _torch()
+        self.store, self.k, self.device = store, k, device
+        self.max_pairs = max(1, int(max_pairs))
+        self.workspace_bytes = dibella_xdrop_workspace_bytes(self.max_pairs, max(store.max_len, 1))
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+        self.pairs = torch.empty((self.max_pairs, 24), dtype=torch.uint8, device=device)
+        self.results = torch.empty((self.max_pairs, 40), dtype=torch.uint8, device=device)
+
+    def upload_pairs(self, pairs: np.ndarray, non_blocking: bool = False):
+        torch = _torch()
+        n = len(pairs)
+        if n > self.max_pairs:
+            raise ValueError("batch of %d seeds exceeds this aligner's capacity %d" % (n, self.max_pairs))
+        if n:
+            src = torch.from_numpy(np.ascontiguousarray(pairs).view(np.uint8).reshape(n, 24))
+            self.pairs[:n].copy_(src, non_blocking=non_blocking)
+        return n
+
+    def run(self, n_pairs: int, scoring, stream=None, sched=None, per_pair: bool = False):
+        """Align the first n_pairs uploaded seeds into self.results (device, async)."""
+        from . import Scoring, dibella_xdrop_batch, dibella_xdrop_per_pair
+        s = scoring if isinstance(scoring, Scoring) else Scoring(*scoring)
+        st = self.store
+        if per_pair:
+            dibella_xdrop_per_pair(st.words, st.word_offsets, st.lengths, st.n_reads, self.pairs, n_pairs,
+                                   self.k, s, self.results, self.workspace, self.workspace_bytes, stream)
+        else:
+            dibella_xdrop_batch(st.words, st.word_offsets, st.lengths, st.n_reads, self.pairs, n_pairs,
+                                self.k, s, self.results, self.workspace, self.workspace_bytes, stream, sched)
+
+    def results_host(self, n_pairs: int) -> np.ndarray:
+        from . import RESULT_DTYPE
+        return self.results[:n_pairs].cpu().numpy().reshape(-1).view(RESULT_DTYPE)
+
+    def align(self, pairs: np.ndarray, scoring, sched=None, per_pair: bool = False) -> np.ndarray:
+        """Upload, align and download one batch (synchronous convenience)."""
+        torch = _torch()
+        n = self.upload_pairs(pairs)
+        self.run(n, scoring, sched=sched, per_pair=per_pair)
+        torch.cuda.synchronize()
+        return self.results_host(n)

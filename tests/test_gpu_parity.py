@@ -1,0 +1,219 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bar: bit-exact on every result field (score, both extension scores, all four
+coordinates, status bits and the evaluated-cell count): the method is integer
+arithmetic with a fixed tie-break, so there is no tolerance to allow.
+"""
+
+import random
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import (NARROW_ALL, WIDE_ALL, assert_same, gpu_align, make_pairs, oracle_align, rc,
+                      reads_to_arrays, schedule)
+
+pytestmark = pytest.mark.gpu
+
+INF = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return workloads.generate("c1_tiny")
+
+
+@pytest.mark.parametrize("X", [7, 25])
+def test_c1_all_pairs(c1, X):
+    sc = (1, -1, -1, X)
+    got = gpu_align(c1.reads, c1.offsets, c1.pairs, 17, sc)
+    exp = oracle_align(c1.reads, c1.offsets, c1.pairs, 17, sc)
+    assert_same(got, exp, "c1 X=%d" % X)
+    assert (got["status"] & 4).sum() == len(workloads.pair_groups(c1.pairs)) - 1
+
+
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "wide"])
+@pytest.mark.parametrize("X", [0, 3, 7, 25])
+def test_every_kernel_form_matches(c1, form, X):
+    """Route every extension to one form; escalations must reproduce the result."""
+    if form == "wide":
+        sched = schedule(**WIDE_ALL)
+    else:
+        sched = schedule(narrow_band_cap=int(form[6:]), **NARROW_ALL)
+    pairs = c1.pairs[:300]
+    sc = (1, -1, -1, X)
+    got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, sched=sched)
+    exp = oracle_align(c1.reads, c1.offsets, pairs, 17, sc)
+    assert_same(got, exp, "%s X=%d" % (form, X))
+
+
+def random_overlap_reads(rng, n_reads, lo, hi, err):
+    genome = "".join(rng.choice("ACGT") for _ in range(hi * 3))
+    reads = []
+    for _ in range(n_reads):
+        L = rng.randint(lo, hi)
+        s = rng.randint(0, len(genome) - L)
+        t = genome[s:s + L]
+        if rng.random() < 0.5:
+            t = rc(t)
+        out = []
+        for ch in t:
+            r = rng.random()
+            if r < err * 0.2:
+                out.append(rng.choice([c for c in "ACGT" if c != ch]))
+            elif r < err * 0.7:
+                out.append(ch)
+                out.append(rng.choice("ACGT"))
+            elif r >= err:
+                out.append(ch)
+        reads.append("".join(out))
+    return reads
+
+
+def shared_kmer_pairs(reads, k, max_pairs, rng):
+    index = {}
+    for r, s in enumerate(reads):
+        for p in range(len(s) - k + 1):
+            km = s[p:p + k]
+            index.setdefault(km, []).append((r, p, 0))
+            index.setdefault(rc(km), []).append((r, p, 1))
+    recs = []
+    for km, occ in index.items():
+        for (ra, pa, oa) in occ:
+            for (rb, pb, ob) in occ:
+                if ra < rb:
+                    recs.append((ra, rb, pa, pb, oa ^ ob))
+    rng.shuffle(recs)
+    recs = recs[:max_pairs]
+    recs.sort()
+    return recs
+
+
+@pytest.mark.parametrize("scoring", [(1, -1, -1), (2, -3, -2), (1, -4, -1), (5, -4, -3), (1, 0, -1)])
+def test_fuzz_medium(scoring):
+    rng = random.Random(hash(scoring) & 0xffff)
+    reads = random_overlap_reads(rng, 30, 200, 2500, 0.12)
+    k = 11
+    recs = shared_kmer_pairs(reads, k, 400, rng)
+    ascii, offs = reads_to_arrays(reads)
+    pairs = make_pairs(recs)
+    for X in (0, 1, 5, 12, 40):
+        sc = scoring + (X,)
+        exp = oracle_align(ascii, offs, pairs, k, sc)
+        for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL)):
+            got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
+            assert_same(got, exp, "scoring %s X=%d" % (sc, X))
+
+
+def test_infinite_x_uses_global_band():
+    """X = infinity: the band is the whole matrix; extensions longer than the
+    shared-memory band (1024 cells) in both reads force the global-memory form."""
+    import paper_2001_10049_gb300 as dib
+    rng = random.Random(3)
+    reads = random_overlap_reads(rng, 6, 1400, 1800, 0.1)
+    k = 9
+    recs = shared_kmer_pairs(reads, k, 100000, rng)
+    recs.sort(key=lambda r: r[2] + r[3])
+    recs = sorted(recs[:4] + rng.sample(recs[4:], 4))
+    ascii, offs = reads_to_arrays(reads)
+    pairs = make_pairs(recs)
+    sc = (1, -1, -1, INF)
+    store = dib.ReadStore.from_ascii(ascii, offs)
+    al = dib.Aligner(store, len(pairs), k=k)
+    got = al.align(pairs, dib.Scoring(*sc))
+    exp = oracle_align(ascii, offs, pairs, k, sc)
+    assert_same(got, exp, "X=inf")
+    assert dib.dibella_batch_counters(al.workspace)["escalated_wide_to_global"] > 0
+
+
+def test_edge_cases():
+    k = 5
+    reads = ["ACGTACGTAC", "ACGTACGTAC", "AAAAAAAAAAAAAAAAAAAA", "CCCCCCCCCCCCCCCCCCCC", "ACG",
+             "GTACGTACGT", "TTTTTAAAAA" * 30, "ACGTT"]
+    recs = [
+        (0, 1, 0, 0, 0),      # seed at the start of both reads (empty left extension)
+        (0, 1, 5, 5, 0),      # seed ending at the read end (empty right extension)
+        (0, 1, 2, 2, 0),
+        (2, 3, 0, 0, 0),      # seed bases mismatch everywhere: status bit 0
+        (2, 2, 3, 9, 0),      # self pair, homopolymer
+        (0, 4, 0, 0, 0),      # read shorter than k: invalid
+        (0, 9, 0, 0, 0),      # read id out of range: invalid
+        (0, 1, 6, 0, 0),      # pos_a + k beyond the read: invalid
+        (0, 1, 0, 0, 2),      # strand out of range: invalid
+        (0, 5, 1, 0, 1),      # reverse strand
+        (6, 6, 0, 150, 0),    # long self alignment at an offset
+        (7, 0, 0, 0, 1),
+    ]
+    ascii, offs = reads_to_arrays(reads)
+    pairs = make_pairs(recs)
+    for X in (0, 2, 7, INF):
+        for M, S, G in ((1, -1, -1), (3, -2, -5)):
+            sc = (M, S, G, X)
+            got = gpu_align(ascii, offs, pairs, k, sc)
+            exp = oracle_align(ascii, offs, pairs, k, sc)
+            assert_same(got, exp, "edge X=%d" % X)
+    assert got["status"][5] == 2 and got["status"][6] == 2 and got["status"][7] == 2 and got["status"][8] == 2
+
+
+def test_empty_batch():
+    reads = ["ACGTACGTACGT"]
+    ascii, offs = reads_to_arrays(reads)
+    got = gpu_align(ascii, offs, make_pairs([]), 5, (1, -1, -1, 7))
+    assert len(got) == 0
+
+
+def test_per_pair_baseline_matches(c1):
+    pairs = c1.pairs[:120]
+    sc = (1, -1, -1, 25)
+    got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, per_pair=True)
+    exp = oracle_align(c1.reads, c1.offsets, pairs, 17, sc)
+    assert_same(got, exp, "per-pair")
+
+
+def test_host_entry_point_and_determinism(c1):
+    import torch
+    import paper_2001_10049_gb300 as dib
+    store = dib.ReadStore.from_ascii(c1.reads, c1.offsets)
+    al = dib.Aligner(store, len(c1.pairs), k=17)
+    sc = dib.Scoring(1, -1, -1, 7)
+    first = al.align(c1.pairs, sc)
+    host_pairs = torch.from_numpy(c1.pairs.view(np.uint8).reshape(-1, 24).copy()).pin_memory()
+    host_res = torch.empty((len(c1.pairs), 40), dtype=torch.uint8).pin_memory()
+    staging = torch.empty(dib.dibella_staging_bytes(len(c1.pairs)), dtype=torch.uint8, device="cuda")
+    dib.dibella_xdrop_batch_host(store.words, store.word_offsets, store.lengths, store.n_reads, host_pairs,
+                                 len(c1.pairs), 17, sc, host_res, staging, al.workspace, al.workspace_bytes)
+    again = host_res.numpy().reshape(-1).view(dib.RESULT_DTYPE)
+    assert first.tobytes() == again.tobytes()
+    for _ in range(3):
+        assert al.align(c1.pairs, sc).tobytes() == first.tobytes()
+
+
+def test_counters_report_routing(c1):
+    import paper_2001_10049_gb300 as dib
+    store = dib.ReadStore.from_ascii(c1.reads, c1.offsets)
+    al = dib.Aligner(store, len(c1.pairs), k=17)
+    al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, **NARROW_ALL))
+    c = dib.dibella_batch_counters(al.workspace)
+    assert c["narrow"] == 2 * len(c1.pairs) and c["wide"] == 0
+    assert c["escalated_narrow_to_wide"] > 0 and c["band_overflow"] == 0
+
+
+def test_c2_full_size_sampled():
+    """The E. coli-sized batch in the bench's launch configuration; a seeded
+    sample of outputs is recomputed one by one by the oracle."""
+    w = workloads.generate("c2_ecoli")
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(len(w.pairs), 3000, replace=False))
+    for X in (7, 25):
+        sc = (1, -1, -1, X)
+        got = gpu_align(w.reads, w.offsets, w.pairs, 17, sc)
+        exp = oracle_align(w.reads, w.offsets, w.pairs[idx], 17, sc)
+        sub = got[idx].copy()
+        sub["status"] &= ~4  # best-of-pair flags depend on the whole run; checked below
+        e2 = exp.copy()
+        e2["status"] &= ~4
+        assert_same(sub, e2, "c2 sample X=%d" % X)
+        g = workloads.pair_groups(w.pairs)
+        assert (got["status"] & 4).sum() == len(g) - 1
+        assert (got["status"] & 8).sum() == 0
