@@ -50,7 +50,16 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-e2e", action="store_true")
+    # profiling / exploration knobs (the defaults are the benchmark)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--xdrops", default=",".join(str(x) for x in XDROPS))
+    ap.add_argument("--sample-pairs", type=int, default=0,
+                    help="align a seeded sample of this many candidate pairs instead of all")
+    ap.add_argument("--schedule", default=None, help="JSON dict overriding the default schedule")
+    args = ap.parse_args()
+    args.xdrops = tuple(int(x) for x in args.xdrops.split(","))
+    return args
 
 
 def dist_setup(args):
@@ -133,30 +142,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, seconds: float):
+def cpu_baseline(w, seconds: float, xdrops):
     """The oracle, as it stands, on the host cores, over a bounded seeded sample
     of the same workload, both X values; scaled to candidate pairs per second."""
     import oracle
     threads = os.cpu_count() or 1
     probe = workloads.sample_pair_groups(w.pairs, 300, seed=17)
     t0 = time.perf_counter()
-    for X in XDROPS:
+    for X in xdrops:
         oracle.xdrop_batch(w.reads, w.offsets, probe, K, 1, -1, -1, X, n_threads=threads)
     dt = time.perf_counter() - t0
     n_groups = max(300, int(300 * seconds / max(dt, 1e-3)))
     sample = workloads.sample_pair_groups(w.pairs, n_groups, seed=18)
     t0 = time.perf_counter()
     cells = 0
-    for X in XDROPS:
+    for X in xdrops:
         r = oracle.xdrop_batch(w.reads, w.offsets, sample, K, 1, -1, -1, X, n_threads=threads)
         cells += int(r["cells"].sum())
     dt = time.perf_counter() - t0
     n_cand = len(workloads.pair_groups(sample)) - 1
-    return {"value": len(XDROPS) * n_cand / dt, "unit": "aligned pairs/s", "cores": threads, "kind": "oracle",
+    return {"value": len(xdrops) * n_cand / dt, "unit": "aligned pairs/s", "cores": threads, "kind": "oracle",
             "gcups": cells / dt / 1e9,
             "sample": "%d candidate pairs (%d seed records) drawn with seed 18 from the %s workload, "
-                      "aligned at X=7 and X=25 by the plain C++ oracle on %d host threads, %.1f s"
-                      % (n_cand, len(sample), WORKLOAD, threads, dt)}
+                      "aligned at X=%s by the plain C++ oracle on %d host threads, %.1f s"
+                      % (n_cand, len(sample), w.name, ",".join(map(str, xdrops)), threads, dt)}
 
 
 def run_reference(args, world, rank):
@@ -202,9 +211,17 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workloads.generate(WORKLOAD)
+    XD = args.xdrops
+    w = workloads.generate(args.workload)
     pairs = w.pairs
+    if args.sample_pairs:
+        pairs = workloads.sample_pair_groups(pairs, args.sample_pairs, seed=29)
     n_seeds = len(pairs)
+    sched = None
+    if args.schedule:
+        d = dib.dibella_get_default_schedule().as_dict()
+        d.update(json.loads(args.schedule))
+        sched = dib.Schedule.from_dict(d)
     n_cand = len(workloads.pair_groups(pairs)) - 1
     store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
     al = dib.Aligner(store, n_seeds, k=K, device=dev)
@@ -217,24 +234,22 @@ def main():
     graphs = {}
     counters = {}
     with torch.cuda.stream(stream):
-        for X in XDROPS:
-            al.run(n_seeds, (1, -1, -1, X), stream=stream)
+        for X in XD:
+            al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
             torch.cuda.synchronize(dev)
             counters[X] = dib.dibella_batch_counters(al.workspace, stream=stream)
-        for X in XDROPS:
+        for X in XD:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                al.run(n_seeds, (1, -1, -1, X), stream=stream)
+                al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
             graphs[X] = g
     torch.cuda.synchronize(dev)
-    cells = {X: int(al_cells) for X, al_cells in
-             ((X, sum(counters[X][c] for c in ("cells_narrow", "cells_wide", "cells_wide_escalated",
-                                                "cells_global"))) for X in XDROPS)}
-    dominant_cells = {X: counters[X]["cells_narrow"] + counters[X]["cells_wide"] for X in XDROPS}
+    cells = {X: sum(counters[X][c] for c in ("cells_narrow", "cells_register", "cells_smem", "cells_global"))
+             for X in XD}
 
     def one_step(record):
         total_ms = 0.0
-        for X in XDROPS:
+        for X in XD:
             with torch.cuda.stream(stream):
                 flush.fill_(X & 0xFF)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -267,7 +282,7 @@ def main():
 
     # Verify the graph replays produced the same results as a direct call.
     res_graph = al.results_host(n_seeds).copy()
-    al.run(n_seeds, (1, -1, -1, XDROPS[-1]), stream=stream)
+    al.run(n_seeds, (1, -1, -1, XD[-1]), stream=stream, sched=sched)
     torch.cuda.synchronize(dev)
     assert al.results_host(n_seeds).tobytes() == res_graph.tobytes(), "graph replay differs from direct call"
 
@@ -276,15 +291,15 @@ def main():
     host_res = torch.empty((n_seeds, 40), dtype=torch.uint8).pin_memory()
     staging = torch.empty(dib.dibella_staging_bytes(n_seeds), dtype=torch.uint8, device=dev)
     e2e_ms = []
-    for it in range(args.warmup + args.steps):
+    for it in range(0 if args.no_e2e else args.warmup + args.steps):
         t0 = time.perf_counter()
-        for X in XDROPS:
+        for X in XD:
             dib.dibella_xdrop_batch_host(store.words, store.word_offsets, store.lengths, store.n_reads,
                                          host_pairs, n_seeds, K, dib.Scoring(1, -1, -1, X), host_res, staging,
-                                         al.workspace, al.workspace_bytes, stream=stream)
+                                         al.workspace, al.workspace_bytes, stream=stream, sched=sched)
         if it >= args.warmup:
             e2e_ms.append(1000 * (time.perf_counter() - t0))
-    e2e_step = float(np.mean(e2e_ms))
+    e2e_step = float(np.mean(e2e_ms)) if e2e_ms else None
 
     # Plain baseline: one launch per seed, on a seeded sample of whole pairs.
     plain = None
@@ -298,17 +313,18 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for X in XDROPS:
+            for X in XD:
                 ps.run(len(sample), (1, -1, -1, X), stream=stream, per_pair=True)
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
-        plain = {"value": len(XDROPS) * n_cand_s / dt, "unit": "aligned pairs/s",
-                 "sample": "%d candidate pairs (%d seed records, seed 23), X=7 and X=25, one kernel launch "
-                           "(one warp) per seed on one stream, no graph" % (n_cand_s, len(sample))}
+        plain = {"value": len(XD) * n_cand_s / dt, "unit": "aligned pairs/s",
+                 "sample": "%d candidate pairs (%d seed records, seed 23), X=%s, one kernel launch "
+                           "(one warp) per seed on one stream, no graph"
+                           % (n_cand_s, len(sample), ",".join(map(str, XD)))}
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        cpu = cpu_baseline(w, args.cpu_seconds)
+        cpu = cpu_baseline(w, args.cpu_seconds, XD)
 
     if rank != 0:
         return
@@ -316,12 +332,17 @@ def main():
     clk = clocks.summary()
     # Roofline of the dominant kernel (the first extend launch): integer ops of
     # the cells it finished / its event-timed duration, per launch.
-    ext_ms = {X: float(np.mean([ph[1] for (x, _, ph) in log if x == X and len(ph) > 1])) for X in XDROPS}
-    batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XDROPS}
-    achieved = float(np.mean([OPS_PER_CELL * dominant_cells[X] / (ext_ms[X] * 1e-3) / 1e12 for X in XDROPS]))
+    # phases: 0 queueing, 1 register form, 2 narrow form, 3 escalations, 4 combine
+    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 5]), axis=0) for X in XD}
+    batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XD}
+    # dominant kernel per X: the longer of the register and narrow launches
+    dom = {X: ("register", 1, "cells_register") if phase[X][1] >= phase[X][2] else ("narrow", 2, "cells_narrow")
+           for X in XD}
+    ext_ms = {X: float(phase[X][dom[X][1]]) for X in XD}
+    achieved = float(np.mean([OPS_PER_CELL * counters[X][dom[X][2]] / (ext_ms[X] * 1e-3) / 1e12 for X in XD]))
     peak_ops = SM_COUNT * INT32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     total_cells = sum(cells.values())
-    value = world * len(XDROPS) * n_cand / (my_ms * 1e-3)
+    value = world * len(XD) * n_cand / (my_ms * 1e-3)
     out = {
         "metric": "aligned pairs/s",
         "value": value,
@@ -335,25 +356,29 @@ def main():
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "genome_bp": w.params["genome_len"], "coverage": w.params["coverage"],
+        "config": {"workload": w.name + (" (sample of %d pairs)" % n_cand if args.sample_pairs else ""),
+                   "genome_bp": w.params["genome_len"], "coverage": w.params["coverage"],
                    "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n_seeds,
-                   "xdrop": list(XDROPS), "scoring": "+1/-1/-1", "k": K,
+                   "xdrop": list(XD), "scoring": "+1/-1/-1", "k": K,
+                   "schedule": (sched or dib.dibella_get_default_schedule()).as_dict(),
                    "l2": "flushed (256 MiB write) before every timed batch",
                    "graph": "one CUDA graph per X (whole dibella_xdrop_batch)",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
         "gcups": total_cells / (my_ms * 1e-3) / 1e9,
         "per_xdrop": {str(X): {"ms": batch_ms[X], "pairs_per_s": n_cand / (batch_ms[X] * 1e-3),
                                "gcups": cells[X] / (batch_ms[X] * 1e-3) / 1e9, "cells": cells[X],
-                               "extend_ms": ext_ms[X], "counters": counters[X]} for X in XDROPS},
+                               "phase_ms": [round(float(v), 3) for v in phase[X]],
+                               "dominant": dom[X][0], "counters": counters[X]} for X in XD},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "extend_kernel<64> (first launch)",
+                     "kernel": ", ".join("X=%d: %s form" % (X, dom[X][0]) for X in XD),
                      "peak_source": "%d SMs x %d INT32 lanes x %.0f MHz (%s sm_max_mhz)"
                                     % (SM_COUNT, INT32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), pk_kind),
                      "ops_per_cell": OPS_PER_CELL},
-        "e2e": {"value": world * len(XDROPS) * n_cand / (e2e_step * 1e-3), "unit": "aligned pairs/s",
-                "h2d_bytes_per_step": len(XDROPS) * n_seeds * 24, "d2h_bytes_per_step": len(XDROPS) * n_seeds * 40},
-        "gpu_launches": args.steps * len(XDROPS) * 8,
+        "e2e": ({"value": world * len(XD) * n_cand / (e2e_step * 1e-3), "unit": "aligned pairs/s",
+                 "h2d_bytes_per_step": len(XD) * n_seeds * 24, "d2h_bytes_per_step": len(XD) * n_seeds * 40}
+                if e2e_step else None),
+        "gpu_launches": args.steps * len(XD) * 8,
         "clocks": clk,
         "plain_per_pair": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,

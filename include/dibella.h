@@ -119,9 +119,11 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  * on the schedule; only speed does.  Every extension first goes to one of:
  *   narrow  one thread per extension, band in per-thread shared memory of
  *           narrow_band_cap cells (32, 48 or 64);
- *   wide    one warp per extension, band in shared memory of 1024 cells;
- * an extension whose band outgrows its kernel is re-run by the next wider
- * one (narrow -> wide -> global-memory band sized from the workspace).
+ *   wide    one warp per extension, band in registers: wide_slots (16 or 32)
+ *           chunks of 32 cells, of which wide_slots - 2 hold the band;
+ * an extension whose band outgrows its form is re-run from the start by a
+ * warp with a 4096-cell shared-memory band, and beyond that by a warp whose
+ * band lives in the workspace (sized by max_read_len: it cannot overflow).
  * An extension is routed to narrow when xdrop <= narrow_max_xdrop and
  * min(remaining A, remaining B) <= narrow_max_len.  Work is ordered by
  * n_buckets length buckets (longest first); bucket b holds keys below
@@ -131,6 +133,7 @@ typedef struct {
   int32_t narrow_max_xdrop;
   int32_t narrow_max_len;
   int32_t narrow_band_cap;
+  int32_t wide_slots;
   int32_t wide_blocks_per_sm;     /* 0 = occupancy maximum                   */
   int32_t narrow_blocks_per_sm;   /* 0 = occupancy maximum                   */
   int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
@@ -211,23 +214,22 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
 
 /* ---- diagnostics ------------------------------------------------------ */
 /* Phase timing: when enabled, dibella_xdrop_batch records CUDA events on
- * `stream` at five points: before expand, after expand/scan/scatter, after the
- * first extend launch, after the escalation launches, after combine.  Under
+ * `stream` at six points around its phases.  Under
  * stream capture they are recorded as external events, so a replayed CUDA
  * graph records them too.  dibella_phase_times() synchronises on the last
- * event and writes up to n_max phase durations in ms (queueing, extend,
- * escalations, combine); returns the count written.  Enable it before any
+ * event and writes up to n_max phase durations in ms: queueing (expand, scan,
+ * scatter), wide register form, narrow form, escalations (shared-memory and
+ * global forms), combine; returns the count written.  Enable it before any
  * capture (it creates the events). */
 int dibella_enable_phase_timing(int enable);
 int dibella_phase_times(float* ms_out, int n_max);
 
 /* Counters of the last batch run with `workspace` (synchronises `stream`):
- * out[0] extensions routed narrow, out[1] routed wide, out[2] escalated
- * narrow->wide, out[3] escalated wide->global, out[4] band overflows,
- * out[5..8] evaluated cells of the extensions finished by the narrow form,
- * the wide form of the first extend launch, the wide form of the escalation
- * launch and the global-band form.  Returns the number written (<= n_max,
- * at most 9), or a negative status. */
+ * out[0] extensions routed narrow, out[1] routed wide, out[2..4] extensions
+ * that outgrew the narrow / register / shared-memory form, out[5] band
+ * overflows, out[6..9] evaluated cells of the extensions finished by the
+ * narrow, register, shared-memory and global-band forms.  Returns the number
+ * written (<= n_max, at most 10), or a negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */

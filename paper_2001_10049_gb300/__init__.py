@@ -51,20 +51,22 @@ class Scoring(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("narrow_max_xdrop", ctypes.c_int32), ("narrow_max_len", ctypes.c_int32),
-                ("narrow_band_cap", ctypes.c_int32), ("wide_blocks_per_sm", ctypes.c_int32),
+                ("narrow_band_cap", ctypes.c_int32), ("wide_slots", ctypes.c_int32),
+                ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
                 ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
-                "narrow_band_cap": self.narrow_band_cap, "wide_blocks_per_sm": self.wide_blocks_per_sm,
+                "narrow_band_cap": self.narrow_band_cap, "wide_slots": self.wide_slots,
+                "wide_blocks_per_sm": self.wide_blocks_per_sm,
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
                 "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)]}
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
         s = cls()
-        for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_blocks_per_sm",
+        for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_slots", "wide_blocks_per_sm",
                     "narrow_blocks_per_sm", "n_buckets"):
             setattr(s, key, int(d[key]))
         bounds = list(d.get("bucket_bounds", []))
@@ -239,12 +241,12 @@ def dibella_phase_times(n_max: int = 8) -> list[float]:
 
 
 def dibella_batch_counters(workspace, stream=None) -> dict:
-    buf = (ctypes.c_int64 * 9)()
-    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 9)
+    buf = (ctypes.c_int64 * 10)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 10)
     if n < 0:
         _check(n, "dibella_batch_counters")
-    keys = ["narrow", "wide", "escalated_narrow_to_wide", "escalated_wide_to_global", "band_overflow",
-            "cells_narrow", "cells_wide", "cells_wide_escalated", "cells_global"]
+    keys = ["narrow", "wide", "escalated_narrow", "escalated_register", "escalated_smem", "band_overflow",
+            "cells_narrow", "cells_register", "cells_smem", "cells_global"]
     return {keys[i]: int(buf[i]) for i in range(n)}
 
 

@@ -72,7 +72,8 @@ struct Counters {
   unsigned int head[4];   // pop cursors
   unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
-  unsigned int stat[8];   // 0 narrow routed, 1 wide routed, 2 esc1, 3 esc2, 4 overflow
+  unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / register /
+                          // shared-memory form, band overflows
   unsigned long long cells[4];  // cells of finished extensions: narrow, wide pass 1, wide pass 2, global
 };
 
@@ -96,18 +97,15 @@ struct ExtendParams {
   const Item* __restrict__ items;
   ExtOut* ext;
   Counters* cnt;
-  const int* wide_q;
-  int wide_q_id;     // which head/tail pair belongs to wide_q
-  const int* narrow_q;
-  int narrow_q_id;   // -1: no narrow phase
-  int* esc_q;        // wide overflow goes here (global kernel) ...
+  const int* wide_q;  // queue popped one item per warp (wide forms)
+  int wide_q_id;      // its head/tail index in Counters
+  const int* narrow_q;  // queue popped one item per lane (narrow form)
+  int narrow_q_id;
+  int* esc_q;         // where extensions that outgrow the form go
   int esc_q_id;
-  int* esc_narrow_q; // narrow overflow goes here (second extend launch)
-  int esc_narrow_q_id;
   Scoring sc;
   int* gband;
   int gcap;
-  int wide_cells_slot;  // Counters::cells index credited by this launch's wide phase
 };
 
 __device__ __forceinline__ uint32_t base_window(const uint32_t* __restrict__ words, long long idx) {
@@ -202,6 +200,140 @@ __device__ bool extend_warp(const uint32_t* __restrict__ words, const Item& it, 
     H2 = H1;
     H1 = H0;
     H0 = t;
+  }
+  if (lane == 0) {
+    out->best = best;
+    out->i_end = bi;
+    out->j_end = bj;
+    out->status = 0;
+    out->cells = cells;
+  }
+  __syncwarp();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Register form: one warp per extension, the band held in registers.
+// Cells are grouped in chunks of 32 consecutive i (lane l of chunk c holds
+// cell i = 32c + l).  NC register slots hold chunks cbase .. cbase+NC-1;
+// slot 0 is a guard below the band (chunk lo/32 - 1) and the band plus the
+// chunk holding hi+1 must fit in slots 1..NC-1, else the extension is handed
+// to a wider form.  Per lane and slot: H (antidiagonal d-1), Up (the up
+// neighbour read on d-1, i.e. H(d-2, i-1), the diagonal predecessor on d) and
+// Bb (b base of the cell on d-1); the a base of every slot is packed 2 bits
+// per slot in one register.  Moving from d-1 to d, every cell takes its up
+// neighbour and its b base from the cell below (lane - 1, or lane 31 of the
+// slot below for lane 0), so a chunk costs two shuffles and no memory access;
+// slots are processed top down so the slot below still holds d-1.  The lowest
+// chunk's lane 0 reads its new b base from memory.
+__device__ __forceinline__ int base_of(const uint32_t* __restrict__ words, long long idx) {
+  return (int)((__ldg(words + (idx >> 4)) >> ((unsigned)(idx & 15) * 2u)) & 3u);
+}
+
+template <int NC>
+__device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, const Scoring sc,
+                           ExtOut* out) {
+  const int lane = threadIdx.x & 31;
+  const int src_lane = (lane + 31) & 31;
+  const bool top_lane = lane == 31;
+  const int m = it.m, n = it.n;
+  const long long a_lo = it.a0 - 1;   // store index of a[i-1] is a_lo + i
+  const long long b_lo = it.b0 + 1;   // store index of b[d-i-1] is b_lo - d + i
+  int H[NC], Up[NC], Bb[NC];
+  unsigned Aall = 0;
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    H[s] = kNeg;
+    Up[s] = kNeg;
+    Bb[s] = 0;
+  }
+  // Antidiagonal 0: cell (0,0) = 0 in chunk 0 (slot 1); slot 0 guards chunk -1.
+  int cbase = -1, ctop = 0;
+  if (lane == 0) H[1] = 0;
+  Aall = (unsigned)base_of(words, a_lo + lane) << 2;
+  Bb[1] = base_of(words, b_lo + lane);  // b base of cell i on "d = 0": b_lo - 0 + i
+  int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  long long cells = 0;
+  for (int d = 1; d <= m + n; ++d) {
+    const int lo = max(live_lo, d - n);
+    const int hi = min(min(live_hi + 1, d), m);
+    const int c0 = lo >> 5;
+    while (cbase < c0 - 1) {  // keep slot 0 = chunk c0 - 1
+#pragma unroll
+      for (int s = 0; s + 1 < NC; ++s) {
+        H[s] = H[s + 1];
+        Up[s] = Up[s + 1];
+        Bb[s] = Bb[s + 1];
+      }
+      H[NC - 1] = kNeg;
+      Up[NC - 1] = kNeg;
+      Aall >>= 2;
+      ++cbase;
+    }
+    const int cneed = (hi + 1) >> 5;
+    if (cneed - cbase > NC - 1) return false;
+    if (cneed > ctop) {  // at most one new chunk per antidiagonal
+      const int snew = cneed - cbase;
+      const int ab = base_of(words, a_lo + 32 * cneed + lane);
+      const int bb = base_of(words, b_lo + 1 - d + 32 * cneed + lane);
+#pragma unroll
+      for (int s = 1; s < NC; ++s) {
+        if (s == snew) {
+          H[s] = kNeg;
+          Up[s] = kNeg;
+          Bb[s] = bb;
+        }
+      }
+      Aall = (Aall & ~(3u << (2 * snew))) | ((unsigned)ab << (2 * snew));
+    }
+    ctop = cneed;
+    const int thr = best - sc.X;
+    const int bfresh = base_of(words, b_lo - d + 32 * c0);  // lane 0 of chunk c0
+    const unsigned span = (unsigned)(hi - lo);
+    int vmax = kNeg, first = 0, last = -1;
+#pragma unroll
+    for (int s = NC - 1; s >= 1; --s) {
+      const int c = cbase + s;
+      if (c <= ctop) {
+        const int u = __shfl_sync(kFull, top_lane ? H[s - 1] : H[s], src_lane);
+        int bn = __shfl_sync(kFull, top_lane ? Bb[s - 1] : Bb[s], src_lane);
+        if (s == 1 && lane == 0) bn = bfresh;
+        const int i = 32 * c + lane;
+        const int a = (int)((Aall >> (2 * s)) & 3u);
+        const int sub = (a ^ bn) == 3 ? sc.M : sc.S;
+        int h = max(max(u, H[s]) + sc.G, Up[s] + sub);
+        const bool live = ((unsigned)(i - lo) <= span) && h >= thr;
+        h = live ? h : kNeg;
+        Up[s] = u;
+        H[s] = h;
+        Bb[s] = bn;
+        vmax = max(vmax, h);
+        const unsigned bl = __ballot_sync(kFull, live);
+        if (bl) {
+          first = 32 * c + __ffs(bl) - 1;
+          if (last < 0) last = 32 * c + 31 - __clz(bl);
+        }
+      }
+    }
+    H[0] = kNeg;
+    cells += hi - lo + 1;
+    vmax = __reduce_max_sync(kFull, vmax);
+    if (vmax == kNeg) break;
+    if (vmax > best) {
+      int cand = INT32_MAX;
+#pragma unroll
+      for (int s = 1; s < NC; ++s) {
+        if (cbase + s <= ctop) {
+          const unsigned bl = __ballot_sync(kFull, H[s] == vmax);
+          if (bl) cand = min(cand, 32 * (cbase + s) + __ffs(bl) - 1);
+        }
+      }
+      best = vmax;
+      bi = cand;
+      bj = d - cand;
+    }
+    live_lo = first;
+    live_hi = last;
   }
   if (lane == 0) {
     out->best = best;
@@ -326,40 +458,65 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
 }
 
 // ---------------------------------------------------------------------------
-// Persistent extension kernel.  Each warp owns 2*WT*32 ints of shared memory,
-// used either as 32 narrow lanes or as one wide band of the largest power of
-// two not above a third of it.
-template <int WT>
-__global__ void __launch_bounds__(kBlockThreads) extend_kernel(ExtendParams p) {
+// Persistent kernels.  Each pops items from one queue until it is empty;
+// an extension whose band outgrows the form is appended to p.esc_q.
+
+// Register form, one warp per extension.
+template <int NC>
+__global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p) {
+  const int lane = threadIdx.x & 31;
+  const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  for (;;) {
+    const unsigned q = pop_warp(p.cnt, p.wide_q_id);
+    if (q >= tail) break;
+    const int item = p.wide_q[q];
+    const Item it = p.items[item];
+    if (!extend_reg<NC>(p.words, it, p.sc, p.ext + item)) {
+      if (lane == 0) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        p.esc_q[s] = item;
+        atomicAdd(&p.cnt->stat[3], 1u);
+      }
+    } else if (lane == 0) {
+      atomicAdd(&p.cnt->cells[1], (unsigned long long)p.ext[item].cells);
+    }
+    __syncwarp();
+  }
+}
+
+// Shared-memory form, one warp per extension, band of kSmemCap cells.
+constexpr int kSmemCap = 4096;
+constexpr int kSmemWarps = 2;
+__global__ void __launch_bounds__(kSmemWarps * 32) wide_smem_kernel(ExtendParams p) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  int* wbase = smem + warp * (2 * WT * 32);
-  constexpr int kWideCap = (2 * WT * 32 / 3) >= 1024 ? 1024 : ((2 * WT * 32 / 3) >= 512 ? 512 : 256);
-
-  // Phase 1: wide items, one warp each, longest first.
-  if (p.wide_q != nullptr) {
-    const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
-    for (;;) {
-      const unsigned q = pop_warp(p.cnt, p.wide_q_id);
-      if (q >= tail) break;
-      const int item = p.wide_q[q];
-      const Item it = p.items[item];
-      if (!extend_warp<false>(p.words, it, p.sc, wbase, kWideCap, p.ext + item)) {
-        if (lane == 0) {
-          const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-          p.esc_q[s] = item;
-          atomicAdd(&p.cnt->stat[3], 1u);
-        }
-      } else if (lane == 0) {
-        atomicAdd(&p.cnt->cells[p.wide_cells_slot], (unsigned long long)p.ext[item].cells);
+  int* arr = smem + (threadIdx.x >> 5) * 3 * kSmemCap;
+  const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  for (;;) {
+    const unsigned q = pop_warp(p.cnt, p.wide_q_id);
+    if (q >= tail) break;
+    const int item = p.wide_q[q];
+    const Item it = p.items[item];
+    if (!extend_warp<false>(p.words, it, p.sc, arr, kSmemCap, p.ext + item)) {
+      if (lane == 0) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        p.esc_q[s] = item;
+        atomicAdd(&p.cnt->stat[4], 1u);
       }
-      __syncwarp();
+    } else if (lane == 0) {
+      atomicAdd(&p.cnt->cells[2], (unsigned long long)p.ext[item].cells);
     }
+    __syncwarp();
   }
-  if (p.narrow_q == nullptr) return;
+}
 
-  // Phase 2: narrow items, one lane each; lanes refill independently.
+// Narrow form: one lane per extension; lanes refill independently.  Each warp
+// owns 2*WT*32 ints of shared memory (see NarrowLane).
+template <int WT>
+__global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
+  extern __shared__ int smem[];
+  const int lane = threadIdx.x & 31;
+  int* wbase = smem + (threadIdx.x >> 5) * (2 * WT * 32);
   const unsigned ntail = *((volatile unsigned*)&p.cnt->tail[p.narrow_q_id]);
   NarrowLane<WT> L;
   bool active = false, exhausted = false;
@@ -401,8 +558,8 @@ __global__ void __launch_bounds__(kBlockThreads) extend_kernel(ExtendParams p) {
         atomicAdd(&p.cnt->cells[0], (unsigned long long)L.cells);
         active = false;
       } else if (r == 2) {
-        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_narrow_q_id], 1u);
-        p.esc_narrow_q[s] = L.item;
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        p.esc_q[s] = L.item;
         atomicAdd(&p.cnt->stat[2], 1u);
         active = false;
       }
@@ -425,7 +582,7 @@ __global__ void __launch_bounds__(kBlockThreads) global_kernel(ExtendParams p) {
         ExtOut o;
         o.best = 0; o.i_end = 0; o.j_end = 0; o.status = DIBELLA_RES_BAND_OVERFLOW; o.cells = 0;
         p.ext[item] = o;
-        atomicAdd(&p.cnt->stat[4], 1u);
+        atomicAdd(&p.cnt->stat[5], 1u);
       }
     } else if ((threadIdx.x & 31) == 0) {
       atomicAdd(&p.cnt->cells[3], (unsigned long long)p.ext[item].cells);
@@ -642,14 +799,15 @@ thread_local std::string g_last_error;
 std::mutex g_mu;
 dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/16, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/64,
-    /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0, /*n_buckets=*/6,
+    /*wide_slots=*/16, /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0, /*n_buckets=*/6,
     {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
 
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
-  int blocks[3] = {0, 0, 0};   // extend_kernel<32/48/64> blocks per SM at full smem
-  int global_blocks = 0;
+  int narrow_blocks[3] = {0, 0, 0};  // narrow_kernel<32/48/64> blocks per SM
+  int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
+  int smem_blocks = 0;               // wide_smem_kernel blocks per SM
 };
 std::mutex g_dev_mu;
 DeviceInfo g_dev[64];
@@ -703,8 +861,20 @@ int gcap_from_workspace(long long n_pairs, long long bytes) {
 }
 
 template <int WT>
-size_t extend_smem() {
+size_t narrow_smem() {
   return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(int);
+}
+constexpr size_t kWideSmemBytes = (size_t)kSmemWarps * 3 * kSmemCap * sizeof(int);
+
+int occupancy(int* out, const void* fn, int threads, size_t smem) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, threads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (*out < 1) *out = 1;
+  return DIBELLA_OK;
 }
 
 int device_info(DeviceInfo** out) {
@@ -717,16 +887,14 @@ int device_info(DeviceInfo** out) {
   if (!D.ready) {
     e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    const void* fns[3] = {(const void*)extend_kernel<32>, (const void*)extend_kernel<48>,
-                          (const void*)extend_kernel<64>};
-    const size_t sm[3] = {extend_smem<32>(), extend_smem<48>(), extend_smem<64>()};
-    for (int v = 0; v < 3; ++v) {
-      e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[v]);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.blocks[v], fns[v], kBlockThreads, sm[v]);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-      if (D.blocks[v] < 1) D.blocks[v] = 1;
-    }
+    int rc = DIBELLA_OK;
+    if ((rc = occupancy(&D.narrow_blocks[0], (const void*)narrow_kernel<32>, kBlockThreads, narrow_smem<32>())) ||
+        (rc = occupancy(&D.narrow_blocks[1], (const void*)narrow_kernel<48>, kBlockThreads, narrow_smem<48>())) ||
+        (rc = occupancy(&D.narrow_blocks[2], (const void*)narrow_kernel<64>, kBlockThreads, narrow_smem<64>())) ||
+        (rc = occupancy(&D.reg_blocks[0], (const void*)wide_reg_kernel<16>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.reg_blocks[1], (const void*)wide_reg_kernel<32>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.smem_blocks, (const void*)wide_smem_kernel, kSmemWarps * 32, kWideSmemBytes)))
+      return rc;
     D.ready = true;
   }
   *out = &D;
@@ -735,6 +903,7 @@ int device_info(DeviceInfo** out) {
 
 int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
+  if (s.wide_slots != 16 && s.wide_slots != 32) return DIBELLA_EINVAL;
   if (s.n_buckets < 1 || s.n_buckets > DIBELLA_MAX_BUCKETS) return DIBELLA_EINVAL;
   if (s.wide_blocks_per_sm < 0 || s.narrow_blocks_per_sm < 0) return DIBELLA_EINVAL;
   for (int b = 1; b < s.n_buckets - 1; ++b)
@@ -772,16 +941,67 @@ void record(cudaStream_t st, int idx) {
   g_ev_count = idx + 1;
 }
 
-template <int WT>
-cudaError_t launch_extend(int grid, cudaStream_t st, const ExtendParams& ep) {
-  extend_kernel<WT><<<grid, kBlockThreads, extend_smem<WT>(), st>>>(ep);
+cudaError_t launch_narrow(int wt, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (wt == 32)
+    narrow_kernel<32><<<grid, kBlockThreads, narrow_smem<32>(), st>>>(ep);
+  else if (wt == 48)
+    narrow_kernel<48><<<grid, kBlockThreads, narrow_smem<48>(), st>>>(ep);
+  else
+    narrow_kernel<64><<<grid, kBlockThreads, narrow_smem<64>(), st>>>(ep);
   return cudaGetLastError();
 }
 
-cudaError_t launch_extend_any(int wt, int grid, cudaStream_t st, const ExtendParams& ep) {
-  if (wt == 32) return launch_extend<32>(grid, st, ep);
-  if (wt == 48) return launch_extend<48>(grid, st, ep);
-  return launch_extend<64>(grid, st, ep);
+cudaError_t launch_wide_reg(int slots, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (slots == 16)
+    wide_reg_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
+  else
+    wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+  return cudaGetLastError();
+}
+
+// All extension launches of one batch: register form on the wide queue,
+// narrow form on the narrow queue (both escalate to Esc1), shared-memory
+// form on Esc1 (escalates to Esc2), global-band form on Esc2.
+int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, ExtendParams ep, int* const q[4],
+                      cudaStream_t st) {
+  const int wt = sch.narrow_band_cap;
+  const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
+  int nb = D.narrow_blocks[vi];
+  if (sch.narrow_blocks_per_sm > 0) nb = std::min(nb, sch.narrow_blocks_per_sm);
+  int rb = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
+  if (sch.wide_blocks_per_sm > 0) rb = std::min(rb, sch.wide_blocks_per_sm);
+  cudaError_t e;
+
+  ep.wide_q = q[kQWide];
+  ep.wide_q_id = kQWide;
+  ep.narrow_q = nullptr;
+  ep.narrow_q_id = -1;
+  ep.esc_q = q[kQEsc1];
+  ep.esc_q_id = kQEsc1;
+  if ((e = launch_wide_reg(sch.wide_slots, D.sms * rb, st, ep)) != cudaSuccess)
+    return cuda_fail(e, "wide_reg launch");
+  record(st, 2);
+
+  ep.wide_q = nullptr;
+  ep.narrow_q = q[kQNarrow];
+  ep.narrow_q_id = kQNarrow;
+  if ((e = launch_narrow(wt, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
+  record(st, 3);
+
+  ep.wide_q = q[kQEsc1];
+  ep.wide_q_id = kQEsc1;
+  ep.narrow_q = nullptr;
+  ep.esc_q = q[kQEsc2];
+  ep.esc_q_id = kQEsc2;
+  wide_smem_kernel<<<D.sms * D.smem_blocks, kSmemWarps * 32, kWideSmemBytes, st>>>(ep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_smem launch");
+
+  ep.wide_q = q[kQEsc2];
+  ep.wide_q_id = kQEsc2;
+  global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
+  record(st, 4);
+  return DIBELLA_OK;
 }
 
 int expand_and_queue(const uint32_t* words, const int64_t* offs, const int32_t* lens, int64_t n_reads,
@@ -904,42 +1124,10 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.gcap = gcap;
   int* q[4];
   for (int i = 0; i < 4; ++i) q[i] = (int*)(ws + L.queue[i]);
-  const int wt = sch.narrow_band_cap;
-  const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
-  int bps = D->blocks[vi];
-  if (sch.narrow_blocks_per_sm > 0) bps = std::min(bps, sch.narrow_blocks_per_sm);
-  const int grid = D->sms * bps;
-
-  // Pass 1: wide queue, then narrow queue; escalations to Esc1 / Esc2.
-  ep.wide_q = q[kQWide];
-  ep.wide_q_id = kQWide;
-  ep.narrow_q = q[kQNarrow];
-  ep.narrow_q_id = kQNarrow;
-  ep.esc_q = q[kQEsc2];
-  ep.esc_q_id = kQEsc2;
-  ep.esc_narrow_q = q[kQEsc1];
-  ep.esc_narrow_q_id = kQEsc1;
-  ep.wide_cells_slot = 1;
-  cudaError_t e = launch_extend_any(wt, grid, st, ep);
-  if (e != cudaSuccess) return cuda_fail(e, "extend launch");
-  record(st, 2);
-  // Pass 2: narrow->wide escalations (wide form only).
-  ep.wide_q = q[kQEsc1];
-  ep.wide_q_id = kQEsc1;
-  ep.narrow_q = nullptr;
-  ep.narrow_q_id = -1;
-  ep.wide_cells_slot = 2;
-  e = launch_extend_any(wt, grid, st, ep);
-  if (e != cudaSuccess) return cuda_fail(e, "extend launch (escalation)");
-  // Pass 3: wide->global escalations.
-  ep.wide_q = q[kQEsc2];
-  ep.wide_q_id = kQEsc2;
-  global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "global launch");
-  record(st, 3);
+  rc = launch_extensions(*D, sch, ep, q, st);
+  if (rc != DIBELLA_OK) return rc;
   rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
-  record(st, 4);
+  record(st, 5);
   return rc;
 }
 
@@ -1046,10 +1234,10 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
   e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const int64_t v[9] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4],
-                        (int64_t)c.cells[0], (int64_t)c.cells[1], (int64_t)c.cells[2],
-                        (int64_t)c.cells[3]};
-  int n = std::min(n_max, 9);
+  const int64_t v[10] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
+                         (int64_t)c.cells[0], (int64_t)c.cells[1], (int64_t)c.cells[2],
+                         (int64_t)c.cells[3]};
+  int n = std::min(n_max, 10);
   for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
 }
