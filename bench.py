@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--sample-pairs", type=int, default=0,
                     help="align a seeded sample of this many candidate pairs instead of all")
     ap.add_argument("--schedule", default=None, help="JSON dict overriding the default schedule")
+    ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve"], default="batch",
+                    help="batch: the benchmark line (E. coli-sized, X=7 and 25); tune: uneven-length batch, "
+                         "fixed vs autotuned schedule; stream: repeat-rich pairs streamed in chunks; "
+                         "serve: continuous-batching request loop at three offered loads")
+    ap.add_argument("--chunk-pairs", type=int, default=4_000_000)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
     args = ap.parse_args()
     args.xdrops = tuple(int(x) for x in args.xdrops.split(","))
     return args
@@ -200,11 +207,183 @@ def run_reference(args, world, rank):
     }))
 
 
+def _time_direct(torch, al, n, scoring, stream, sched, reps):
+    """Median CUDA-event time (ms) of `reps` direct dibella_xdrop_batch calls
+    (L2 flushed before each), after one untimed call."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=al.workspace.device)
+    times = []
+    for r in range(reps + 1):
+        with torch.cuda.stream(stream):
+            flush.fill_(r & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            al.run(n, scoring, stream=stream, sched=sched)
+            e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def mode_tune(args):
+    """Uneven batch (log-uniform 500 bp - 100 kb reads, per-read error 5-35%,
+    X = 50): the library's default schedule against the schedule its autotuner
+    picks on a 10% sample of the candidate pairs."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    dev = torch.device("cuda", 0)
+    w = workloads.generate("c3_uneven")
+    pairs = w.pairs
+    n = len(pairs)
+    X = 50
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    al = dib.Aligner(store, n, k=K, device=dev)
+    al.upload_pairs(pairs)
+    stream = torch.cuda.Stream(device=dev)
+    sc = dib.Scoring(1, -1, -1, X)
+    fixed = dib.dibella_get_default_schedule()
+    with ClockSampler(0) as clocks:
+        fixed_ms = _time_direct(torch, al, n, sc, stream, fixed, args.steps)
+        c_fixed = dib.dibella_batch_counters(al.workspace, stream=stream)
+        sample = workloads.sample_pair_groups(pairs, max(1, (len(workloads.pair_groups(pairs)) - 1) // 10), seed=31)
+        tal = dib.Aligner(store, len(sample), k=K, device=dev)
+        tal.upload_pairs(sample)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            best, best_ms, tried = dib.dibella_autotune(store.words, store.word_offsets, store.lengths, store.n_reads,
+                                                        tal.pairs, len(sample), K, sc, tal.results, tal.workspace,
+                                                        tal.workspace_bytes, stream=stream, repeats=2)
+        tune_s = time.perf_counter() - t0
+        tuned_ms = _time_direct(torch, al, n, sc, stream, best, args.steps)
+    c_tuned = dib.dibella_batch_counters(al.workspace, stream=stream)
+    cells = sum(c_tuned[c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global"))
+    n_cand = len(workloads.pair_groups(pairs)) - 1
+    print(json.dumps({
+        "metric": "aligned pairs/s", "mode": "tune", "unit": "aligned pairs/s", "n_gpus": 1,
+        "value": n_cand / (tuned_ms * 1e-3), "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "c3_uneven", "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n,
+                   "extensions": 2 * n, "xdrop": X, "scoring": "+1/-1/-1", "k": K, "steps": args.steps,
+                   "l2": "flushed (256 MiB write) before every timed batch"},
+        "fixed": {"schedule": fixed.as_dict(), "ms": fixed_ms, "pairs_per_s": n_cand / (fixed_ms * 1e-3),
+                  "gcups": cells / (fixed_ms * 1e-3) / 1e9, "counters": c_fixed},
+        "tuned": {"schedule": best.as_dict(), "ms": tuned_ms, "pairs_per_s": n_cand / (tuned_ms * 1e-3),
+                  "gcups": cells / (tuned_ms * 1e-3) / 1e9, "counters": c_tuned, "sample_ms": best_ms,
+                  "schedules_tried": tried, "tuning_s": tune_s,
+                  "sample": "%d candidate pairs (10%%, seed 31)" % (len(workloads.pair_groups(sample)) - 1)},
+        "speedup_tuned_vs_fixed": fixed_ms / tuned_ms,
+        "clocks": clocks.summary(),
+    }))
+
+
+def mode_stream(args):
+    """Repeat-rich batch (genome with repeat families and tandem arrays, 40x,
+    multiplicity [2, 12], X = 15) streamed from pinned host memory in chunks
+    through dibella_xdrop_stream, with the read store resident in HBM.  The
+    genome is 1/20 of the configured 100 Mb (every other rule kept)."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    dev = torch.device("cuda", 0)
+    w = workloads.generate("c4_repeats_small")
+    pairs = w.pairs
+    n = len(pairs)
+    X = 15
+    chunk = min(args.chunk_pairs, n)
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    host_pairs = torch.from_numpy(pairs.view(np.uint8).reshape(n, 24).copy()).pin_memory()
+    host_res = torch.zeros((n, 40), dtype=torch.uint8).pin_memory()
+    wsb = dib.dibella_xdrop_workspace_bytes(chunk, store.max_len)
+    staging = [torch.empty(dib.dibella_staging_bytes(chunk), dtype=torch.uint8, device=dev) for _ in range(2)]
+    ws = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    sc = dib.Scoring(1, -1, -1, X)
+    runs = []
+    with ClockSampler(0) as clocks:
+        for r in range(max(1, args.warmup) + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            n_chunks = dib.dibella_xdrop_stream(store.words, store.word_offsets, store.lengths, store.n_reads,
+                                                host_pairs, n, chunk, K, sc, host_res, staging, ws, wsb, streams)
+            if r >= max(1, args.warmup):
+                runs.append(time.perf_counter() - t0)
+    res = host_res.numpy().reshape(-1).view(dib.RESULT_DTYPE)
+    cells = int(res["cells"].sum())
+    n_cand = len(workloads.pair_groups(pairs)) - 1
+    dt = float(np.median(runs))
+    print(json.dumps({
+        "metric": "aligned pairs/s", "mode": "stream", "value": n_cand / dt, "unit": "aligned pairs/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "int32", "data": "synthetic", "gcups": cells / dt / 1e9,
+        "config": {"workload": "c4_repeats_small (5 Mb genome = 1/20 of the configured 100 Mb)",
+                   "reads": int(w.n_reads), "bases": int(len(w.reads)), "candidate_pairs": n_cand, "seed_records": n,
+                   "chunk_pairs": chunk, "chunks": n_chunks, "xdrop": X, "k": K, "multiplicity": [2, 12],
+                   "store_bytes_hbm": store.nbytes, "h2d_bytes": n * 24, "d2h_bytes": n * 40,
+                   "timing": "wall clock of the whole stream call incl. all copies, median of %d" % len(runs)},
+        "status_counts": {str(k): int(v) for k, v in zip(*np.unique(res["status"], return_counts=True))},
+        "clocks": clocks.summary(),
+    }))
+
+
+def mode_serve(args):
+    """Serving loop over the E. coli-sized read store: Poisson arrivals of
+    requests of 1..4096 candidate pairs (log-uniform) with X in {7, 25, 50};
+    capacity measured with every request present at t = 0, then offered loads of
+    0.5, 0.8 and 0.95 x capacity.  Latency = completion - scheduled arrival."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    from paper_2001_10049_gb300.serving import Request, Server
+    dev = torch.device("cuda", 0)
+    w = workloads.generate(WORKLOAD)
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    srv = Server(store, k=K, arena_bytes=4 << 30, max_batch=65536, n_streams=8, device=dev)
+
+    def make(n, rate, seed):
+        specs = workloads.serving_requests(w.pairs, n, rate_per_s=rate, seed=seed)
+        return [Request(i, t, x, w.pairs[idx]) for i, (t, x, idx) in enumerate(specs)]
+
+    warm = make(min(50, args.serve_warmup), 1e9, 40)
+    for r in warm:
+        r.arrival = 0.0
+    srv.run(warm)
+    sat = make(args.serve_requests, 1e9, 41)
+    for r in sat:
+        r.arrival = 0.0
+    cap = srv.run(sat)
+    mean_pairs = cap["pairs"] / cap["requests"]
+    capacity_rps = cap["pairs_per_s"] / mean_pairs
+    loads = []
+    with ClockSampler(0) as clocks:
+        for i, f in enumerate((0.5, 0.8, 0.95)):
+            reqs = make(args.serve_warmup + args.serve_requests, f * capacity_rps, 50 + i)
+            stats = srv.run(reqs)
+            timed = reqs[args.serve_warmup:]
+            lat = np.array([r.done - r.arrival for r in timed])
+            span = max(r.done for r in timed) - min(r.arrival for r in timed)
+            pairs_timed = sum(len(workloads.pair_groups(r.pairs)) - 1 for r in timed)
+            loads.append({"offered_fraction": f, "offered_req_per_s": f * capacity_rps,
+                          "p50_ms": float(np.percentile(lat, 50, method="nearest") * 1e3),
+                          "p99_ms": float(np.percentile(lat, 99, method="nearest") * 1e3),
+                          "sustained_pairs_per_s": pairs_timed / span, "batches": stats["batches"],
+                          "max_inflight_batches": stats["max_inflight"], "requests_timed": len(timed)})
+    print(json.dumps({
+        "metric": "serve p50/p99 ms", "mode": "serve", "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+        "value": loads[1]["p99_ms"], "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " store", "request_pairs": "log-uniform 1..4096", "xdrop": [7, 25, 50],
+                   "warmup_requests": args.serve_warmup, "timed_requests": args.serve_requests,
+                   "arena_bytes": 4 << 30, "streams": 8, "max_batch_seeds": 65536},
+        "capacity": {"pairs_per_s": cap["pairs_per_s"], "req_per_s": capacity_rps, "mean_pairs_per_request": mean_pairs,
+                     "batches": cap["batches"], "max_inflight": cap["max_inflight"]},
+        "loads": loads, "clocks": clocks.summary(),
+    }))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.mode != "batch":
+        if rank == 0:
+            {"tune": mode_tune, "stream": mode_stream, "serve": mode_serve}[args.mode](args)
         return
     import torch
     import paper_2001_10049_gb300 as dib
@@ -244,7 +423,7 @@ def main():
                 al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
             graphs[X] = g
     torch.cuda.synchronize(dev)
-    cells = {X: sum(counters[X][c] for c in ("cells_narrow", "cells_register", "cells_smem", "cells_global"))
+    cells = {X: sum(counters[X][c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global"))
              for X in XD}
 
     def one_step(record):
@@ -332,11 +511,11 @@ def main():
     clk = clocks.summary()
     # Roofline of the dominant kernel (the first extend launch): integer ops of
     # the cells it finished / its event-timed duration, per launch.
-    # phases: 0 queueing, 1 register form, 2 narrow form, 3 escalations, 4 combine
+    # phases: 0 queueing, 1 narrow form, 2 wide form, 3 escalations, 4 combine
     phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 5]), axis=0) for X in XD}
     batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XD}
     # dominant kernel per X: the longer of the register and narrow launches
-    dom = {X: ("register", 1, "cells_register") if phase[X][1] >= phase[X][2] else ("narrow", 2, "cells_narrow")
+    dom = {X: ("wide", 2, "cells_wide") if phase[X][2] >= phase[X][1] else ("narrow", 1, "cells_narrow")
            for X in XD}
     ext_ms = {X: float(phase[X][dom[X][1]]) for X in XD}
     achieved = float(np.mean([OPS_PER_CELL * counters[X][dom[X][2]] / (ext_ms[X] * 1e-3) / 1e12 for X in XD]))

@@ -90,10 +90,11 @@ typedef struct {
 /* ---- packed read store ------------------------------------------------ */
 /* Layout (Sec. 3: 2 bits per base; A=0 C=1 G=2 T=3, complement = 3 - code):
  * 32-bit words, 16 bases per word, base q of a copy at bits 2*(q%16).
- * The store opens with 4 zero words; then, per read r, its forward copy at
+ * The store opens with 8 zero words; then, per read r, its forward copy at
  * word read_word_offsets[r] (a multiple of 4, i.e. 16-byte aligned) followed
  * immediately by its reverse-complement copy; each copy takes
- * 4*ceil(ceil(len/16)/4) words; the store closes with 4 zero words.
+ * 4*ceil(ceil(len/16)/4) words; the store closes with 8 zero words (the
+ * kernels read up to 128 bases past either end of a copy and ignore them).
  * Holding both orientations lets every extension read both sequences in
  * ascending word order, reverse complement included. */
 
@@ -119,8 +120,11 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  * on the schedule; only speed does.  Every extension first goes to one of:
  *   narrow  one thread per extension, band in per-thread shared memory of
  *           narrow_band_cap cells (32, 48 or 64);
- *   wide    one warp per extension, band in registers: wide_slots (16 or 32)
- *           chunks of 32 cells, of which wide_slots - 2 hold the band;
+ *   wide    one warp per extension, band in registers: wide_slots chunks
+ *           (16, 24 or 32), of which wide_slots - 2 hold the band; a chunk
+ *           is 64 cells packed as int16 pairs when wide_packed is set and
+ *           xdrop <= 8000 (exact: scores are kept relative to a moving base),
+ *           else 32 int32 cells;
  * an extension whose band outgrows its form is re-run from the start by a
  * warp with a 4096-cell shared-memory band, and beyond that by a warp whose
  * band lives in the workspace (sized by max_read_len: it cannot overflow).
@@ -133,7 +137,9 @@ typedef struct {
   int32_t narrow_max_xdrop;
   int32_t narrow_max_len;
   int32_t narrow_band_cap;
-  int32_t wide_slots;
+  int32_t wide_slots;             /* 16, 24, 32, or 0 = 16 if xdrop <= 30     */
+                                  /* else 24                                  */
+  int32_t wide_packed;            /* 1: int16-pair cells when xdrop <= 8000   */
   int32_t wide_blocks_per_sm;     /* 0 = occupancy maximum                   */
   int32_t narrow_blocks_per_sm;   /* 0 = occupancy maximum                   */
   int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
@@ -202,6 +208,24 @@ int dibella_xdrop_batch_host(const uint32_t* packed_words, const int64_t* read_w
                              void* staging, void* workspace, int64_t workspace_bytes,
                              void* stream, const dibella_schedule_t* sched);
 
+/* Stream a host-resident seed set through the GPU in chunks of at most
+ * chunk_pairs records, with the read store resident in HBM (the paper's
+ * streaming of bounded phases, Sec. 4, applied to the alignment tasks).
+ * Chunk ends move back to the previous change of (read_a, read_b), so no
+ * candidate pair is split (EINVAL if one pair has more seeds than a chunk).
+ * Two slots alternate: staging[s] (device, dibella_staging_bytes(chunk_pairs)
+ * bytes, 256-byte aligned), workspace[s] (device, workspace_bytes each, sized
+ * for chunk_pairs) and streams[s]; each chunk's H2D copy, batch and D2H copy
+ * are queued on its slot's stream, so the copies of one chunk overlap the
+ * kernels of the other.  host_pairs / host_results should be pinned.
+ * Synchronises both streams; *n_chunks_out (may be NULL) gets the count. */
+int dibella_xdrop_stream(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                         const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* host_pairs,
+                         int64_t n_pairs, int64_t chunk_pairs, int32_t k, dibella_scoring_t scoring,
+                         dibella_result_t* host_results, void* const* staging, void* const* workspace,
+                         int64_t workspace_bytes, void* const* streams, const dibella_schedule_t* sched,
+                         int64_t* n_chunks_out);
+
 /* Baseline form of the same computation: one kernel launch per seed (one
  * warp, left then right extension, no queues, no graph), all on `stream`.
  * Same arguments and results as dibella_xdrop_batch; used to measure what
@@ -211,6 +235,25 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
                            const dibella_pair_t* pairs, int64_t n_pairs, int32_t k,
                            dibella_scoring_t scoring, dibella_result_t* results,
                            void* workspace, int64_t workspace_bytes, void* stream);
+
+/* ---- autotuning -------------------------------------------------------- */
+/* Pick a schedule for batches like this one: runs dibella_xdrop_batch on the
+ * given (sample) batch with candidate schedules and returns the fastest in
+ * *best_out (median of `repeats` timed runs each, CUDA events on `stream`).
+ * The search is staged: routing threshold between the one-thread and the
+ * one-warp forms x per-thread band chunk (32/48/64), then register slots of
+ * the warp form (16/32), then resident blocks per SM, then length-bucket
+ * bounds; each stage keeps the best so far.  Same arguments as
+ * dibella_xdrop_batch; results hold the last run's output.  Synchronises
+ * `stream`; refused (EINVAL) while `stream` is capturing.  *best_ms_out and
+ * *n_tried_out (either may be NULL) receive the winner's time and the number
+ * of schedules timed.  The paper has no tuner; its Sec. 9 names the cost
+ * differences (read length, X-drop early exit) this one adapts to. */
+int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                     const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                     int64_t n_pairs, int32_t k, dibella_scoring_t scoring, dibella_result_t* results,
+                     void* workspace, int64_t workspace_bytes, void* stream, int32_t repeats,
+                     dibella_schedule_t* best_out, float* best_ms_out, int32_t* n_tried_out);
 
 /* ---- diagnostics ------------------------------------------------------ */
 /* Phase timing: when enabled, dibella_xdrop_batch records CUDA events on
@@ -226,9 +269,9 @@ int dibella_phase_times(float* ms_out, int n_max);
 
 /* Counters of the last batch run with `workspace` (synchronises `stream`):
  * out[0] extensions routed narrow, out[1] routed wide, out[2..4] extensions
- * that outgrew the narrow / register / shared-memory form, out[5] band
+ * that outgrew the narrow / wide / shared-memory form, out[5] band
  * overflows, out[6..9] evaluated cells of the extensions finished by the
- * narrow, register, shared-memory and global-band forms.  Returns the number
+ * narrow, wide (register or packed), shared-memory and global-band forms.  Returns the number
  * written (<= n_max, at most 10), or a negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 

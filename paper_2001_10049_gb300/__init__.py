@@ -52,21 +52,22 @@ class Scoring(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("narrow_max_xdrop", ctypes.c_int32), ("narrow_max_len", ctypes.c_int32),
                 ("narrow_band_cap", ctypes.c_int32), ("wide_slots", ctypes.c_int32),
-                ("wide_blocks_per_sm", ctypes.c_int32),
+                ("wide_packed", ctypes.c_int32), ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
                 ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
                 "narrow_band_cap": self.narrow_band_cap, "wide_slots": self.wide_slots,
-                "wide_blocks_per_sm": self.wide_blocks_per_sm,
+                "wide_packed": self.wide_packed, "wide_blocks_per_sm": self.wide_blocks_per_sm,
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
                 "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)]}
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
         s = cls()
-        for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_slots", "wide_blocks_per_sm",
+        for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_slots", "wide_packed",
+                    "wide_blocks_per_sm",
                     "narrow_blocks_per_sm", "n_buckets"):
             setattr(s, key, int(d[key]))
         bounds = list(d.get("bucket_bounds", []))
@@ -98,7 +99,13 @@ def _lib():
                                      ctypes.POINTER(Schedule)], i32),
             "dibella_xdrop_batch_host": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, vp, i64, vp,
                                           ctypes.POINTER(Schedule)], i32),
+            "dibella_xdrop_stream": ([vp, vp, vp, i64, vp, i64, i64, i32, Scoring, vp, ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(Schedule),
+                                      p64], i32),
             "dibella_xdrop_per_pair": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, i64, vp], i32),
+            "dibella_autotune": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, i64, vp, i32,
+                                  ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_int32)], i32),
             "dibella_enable_phase_timing": ([ctypes.c_int], i32),
             "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
             "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
@@ -219,6 +226,22 @@ def dibella_xdrop_batch_host(packed_words, read_word_offsets, read_lengths, n_re
     _check(rc, "dibella_xdrop_batch_host")
 
 
+def dibella_xdrop_stream(packed_words, read_word_offsets, read_lengths, n_reads: int, host_pairs, n_pairs: int,
+                         chunk_pairs: int, k: int, scoring: Scoring, host_results, staging, workspace,
+                         workspace_bytes: int, streams, sched: Schedule | None = None) -> int:
+    """staging / workspace / streams are pairs (two slots); returns the number of chunks."""
+    st = (ctypes.c_void_p * 2)(*[_ptr(x) for x in staging])
+    ws = (ctypes.c_void_p * 2)(*[_ptr(x) for x in workspace])
+    ss = (ctypes.c_void_p * 2)(*[_stream_handle(x) for x in streams])
+    n_chunks = ctypes.c_int64(0)
+    rc = _lib().dibella_xdrop_stream(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths), n_reads,
+                                     _ptr(host_pairs), n_pairs, chunk_pairs, k, scoring, _ptr(host_results), st, ws,
+                                     workspace_bytes, ss, ctypes.byref(sched) if sched is not None else None,
+                                     ctypes.byref(n_chunks))
+    _check(rc, "dibella_xdrop_stream")
+    return int(n_chunks.value)
+
+
 def dibella_xdrop_per_pair(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs, n_pairs: int,
                            k: int, scoring: Scoring, results, workspace, workspace_bytes: int,
                            stream=None) -> None:
@@ -226,6 +249,20 @@ def dibella_xdrop_per_pair(packed_words, read_word_offsets, read_lengths, n_read
                                        n_reads, _ptr(pairs), n_pairs, k, scoring, _ptr(results),
                                        _ptr(workspace), workspace_bytes, _stream_handle(stream))
     _check(rc, "dibella_xdrop_per_pair")
+
+
+def dibella_autotune(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs, n_pairs: int, k: int,
+                     scoring: Scoring, results, workspace, workspace_bytes: int, stream=None, repeats: int = 2):
+    """Returns (best Schedule, its median ms, number of schedules timed)."""
+    best = Schedule()
+    ms = ctypes.c_float(0)
+    tried = ctypes.c_int32(0)
+    rc = _lib().dibella_autotune(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths), n_reads,
+                                 _ptr(pairs), n_pairs, k, scoring, _ptr(results), _ptr(workspace),
+                                 workspace_bytes, _stream_handle(stream), repeats, ctypes.byref(best),
+                                 ctypes.byref(ms), ctypes.byref(tried))
+    _check(rc, "dibella_autotune")
+    return best, float(ms.value), int(tried.value)
 
 
 def dibella_enable_phase_timing(enable: bool) -> None:
@@ -245,8 +282,8 @@ def dibella_batch_counters(workspace, stream=None) -> dict:
     n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 10)
     if n < 0:
         _check(n, "dibella_batch_counters")
-    keys = ["narrow", "wide", "escalated_narrow", "escalated_register", "escalated_smem", "band_overflow",
-            "cells_narrow", "cells_register", "cells_smem", "cells_global"]
+    keys = ["narrow", "wide", "escalated_narrow", "escalated_wide", "escalated_smem", "band_overflow",
+            "cells_narrow", "cells_wide", "cells_smem", "cells_global"]
     return {keys[i]: int(buf[i]) for i in range(n)}
 
 

@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr int64_t kPadWords = 4;
+constexpr int64_t kPadWords = 8;
 
 inline int64_t copy_words(int64_t len) { return ((len + 15) / 16 + 3) / 4 * 4; }
 

@@ -38,6 +38,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dibella.h"
@@ -68,25 +69,20 @@ struct ExtOut {
 static_assert(sizeof(ExtOut) == 24, "ext out is 24 bytes");
 
 struct Counters {
-  unsigned int tail[4];   // queue sizes: 0 narrow, 1 wide, 2 narrow->wide, 3 wide->global
-  unsigned int head[4];   // pop cursors
+  unsigned int tail[5];   // queue sizes (see the kQ* names)
+  unsigned int head[5];   // pop cursors
+  unsigned int pad_;
   unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
-  unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / register /
+  unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / wide /
                           // shared-memory form, band overflows
   unsigned long long cells[4];  // cells of finished extensions: narrow, wide pass 1, wide pass 2, global
 };
 
-enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQEsc2 = 3 };
-
-struct Workspace {
-  Counters* counters;
-  Item* items;
-  ExtOut* ext;
-  int* queue[4];
-  int* gband;
-  int gcap;
-};
+// Queues: routed narrow / wide; narrow escalations (to the wide form);
+// wide escalations (to the shared-memory form); shared-memory escalations
+// (to the global-band form).
+enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQEsc2 = 3, kQEsc3 = 4, kNumQ = 5 };
 
 struct Scoring {
   int M, S, G, X;
@@ -240,7 +236,9 @@ __device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, c
   const long long a_lo = it.a0 - 1;   // store index of a[i-1] is a_lo + i
   const long long b_lo = it.b0 + 1;   // store index of b[d-i-1] is b_lo - d + i
   int H[NC], Up[NC], Bb[NC];
-  unsigned Aall = 0;
+  // a base of every slot, 2 bits per slot (64-bit once there are more than 16 slots)
+  using AWord = typename std::conditional<(NC > 16), unsigned long long, unsigned>::type;
+  AWord Aall = 0;
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     H[s] = kNeg;
@@ -250,7 +248,7 @@ __device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, c
   // Antidiagonal 0: cell (0,0) = 0 in chunk 0 (slot 1); slot 0 guards chunk -1.
   int cbase = -1, ctop = 0;
   if (lane == 0) H[1] = 0;
-  Aall = (unsigned)base_of(words, a_lo + lane) << 2;
+  Aall = (AWord)base_of(words, a_lo + lane) << 2;
   Bb[1] = base_of(words, b_lo + lane);  // b base of cell i on "d = 0": b_lo - 0 + i
   int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
   long long cells = 0;
@@ -284,7 +282,7 @@ __device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, c
           Bb[s] = bb;
         }
       }
-      Aall = (Aall & ~(3u << (2 * snew))) | ((unsigned)ab << (2 * snew));
+      Aall = (Aall & ~((AWord)3 << (2 * snew))) | ((AWord)ab << (2 * snew));
     }
     ctop = cneed;
     const int thr = best - sc.X;
@@ -299,7 +297,7 @@ __device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, c
         int bn = __shfl_sync(kFull, top_lane ? Bb[s - 1] : Bb[s], src_lane);
         if (s == 1 && lane == 0) bn = bfresh;
         const int i = 32 * c + lane;
-        const int a = (int)((Aall >> (2 * s)) & 3u);
+        const int a = (int)((Aall >> (2 * s)) & 3u);  // s is a compile-time constant
         const int sub = (a ^ bn) == 3 ? sc.M : sc.S;
         int h = max(max(u, H[s]) + sc.G, Up[s] + sub);
         const bool live = ((unsigned)(i - lo) <= span) && h >= thr;
@@ -329,6 +327,248 @@ __device__ bool extend_reg(const uint32_t* __restrict__ words, const Item& it, c
         }
       }
       best = vmax;
+      bi = cand;
+      bj = d - cand;
+    }
+    live_lo = first;
+    live_hi = last;
+  }
+  if (lane == 0) {
+    out->best = best;
+    out->i_end = bi;
+    out->j_end = bj;
+    out->status = 0;
+    out->cells = cells;
+  }
+  __syncwarp();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Packed form: one warp per extension, two cells per 32-bit register.
+// Scores are held as int16 pairs relative to a per-extension base `rb`
+// (rebased when the best score gets 4096 above it), which is exact while
+// X <= kPackedMaxX: every live value then lies within [-X, 4096 + 2*match] of
+// rb and dead cells hold kNeg16 = -16384, far from both int16 limits, so no
+// packed add can wrap.  Chunk c covers cells 64c .. 64c+63; lane l holds cells
+// 64c + 2l (low half) and 64c + 2l + 1 (high half).  Slots, guard and
+// escalation follow the register form.  The a and b bases of every cell are
+// 2-bit fields in NC/8 words per lane (slot s of word w = s/8: low cell at bits
+// 2(s%8), high cell at bits 2(s%8)+16), so one word XOR gives the match bits
+// of 16 cells and one shuffle per word moves every b base to the next cell.
+constexpr int kPackedMaxX = 8000;
+constexpr unsigned kNeg2 = 0xC000C000u;  // kNeg16 in both halves
+constexpr int kRebase = 4096;
+
+__device__ __forceinline__ unsigned pk_pair(int lo, int hi) {
+  return ((unsigned)lo & 0xFFFFu) | ((unsigned)hi << 16);
+}
+__device__ __forceinline__ int pk_lo(unsigned v) { return (int)(short)(v & 0xFFFFu); }
+__device__ __forceinline__ int pk_hi(unsigned v) { return (int)(short)(v >> 16); }
+
+template <int NC>
+__device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, const Scoring sc, ExtOut* out) {
+  static_assert(NC % 8 == 0 && NC >= 8 && NC <= 32, "slots come in words of 8");
+  constexpr int NW = NC / 8;
+  const int lane = threadIdx.x & 31;
+  const int src_lane = (lane + 31) & 31;
+  const bool top_lane = lane == 31;
+  const int m = it.m, n = it.n;
+  const long long a_lo = it.a0 - 1;
+  const long long b_lo = it.b0 + 1;
+  unsigned H[NC], Up[NC], Aw[NW], Bw[NW];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    H[s] = kNeg2;
+    Up[s] = kNeg2;
+  }
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    Aw[w] = 0;
+    Bw[w] = 0;
+  }
+  const unsigned M2 = pk_pair(sc.M, sc.M), S2 = pk_pair(sc.S, sc.S), G2 = pk_pair(sc.G, sc.G);
+  int cbase = -1, ctop = 0, rb = 0;
+  // d = 0: cell (0,0) = 0 at chunk 0 (slot 1), lane 0, low half.
+  if (lane == 0) H[1] = pk_pair(0, -16384);
+  {  // bases of chunk 0 (cells 2l, 2l+1): a[i-1] and b on "d = 0"
+    const int i0 = 2 * lane;
+    const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
+    const unsigned b0b = base_of(words, b_lo + i0), b1b = base_of(words, b_lo + i0 + 1);
+    Aw[0] = (a0b << 2) | (a1b << 18);
+    Bw[0] = (b0b << 2) | (b1b << 18);
+  }
+  int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  long long cells = 0;
+  for (int d = 1; d <= m + n; ++d) {
+    const int lo = max(live_lo, d - n);
+    const int hi = min(min(live_hi + 1, d), m);
+    const int c0 = lo >> 6;
+    while (cbase < c0 - 1) {  // keep slot 0 = chunk c0 - 1
+#pragma unroll
+      for (int s = 0; s + 1 < NC; ++s) {
+        H[s] = H[s + 1];
+        Up[s] = Up[s + 1];
+      }
+      H[NC - 1] = kNeg2;
+      Up[NC - 1] = kNeg2;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const int wn = w + 1 < NW ? w + 1 : w;
+        const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
+        Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
+        Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
+      }
+      ++cbase;
+    }
+    const int cneed = (hi + 1) >> 6;
+    if (cneed - cbase > NC - 1) return false;
+    if (cneed > ctop) {  // activate the chunk holding hi + 1 (at most one per antidiagonal)
+      const int snew = cneed - cbase;
+      const int i0 = 64 * cneed + 2 * lane;
+      const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
+      const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
+      const int sh = 2 * (snew & 7);
+      const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        if (w == (snew >> 3)) {
+          Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
+          Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+        }
+      }
+#pragma unroll
+      for (int s = 1; s < NC; ++s) {
+        if (s == snew) {
+          H[s] = kNeg2;
+          Up[s] = kNeg2;
+        }
+      }
+    }
+    ctop = cneed;
+    // Move every b base to the next cell (cell i takes the base of cell i-1),
+    // for the words that hold active slots, and form their mismatch bits.
+    const int ntop = ctop - cbase;
+    const int wtop = ntop >> 3;
+    unsigned MM[NW];
+    {
+      const int bfresh = base_of(words, b_lo - d + 64 * c0);  // lane 0, low cell of slot 1
+      unsigned prev_top = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        MM[w] = 0;
+        if (w <= wtop) {
+          const unsigned t = __shfl_sync(kFull, Bw[w], src_lane);
+          unsigned lo_new = t >> 16;                                  // lane-1's high cells
+          const unsigned lo_lane0 = ((t >> 14) & 0xFFFCu) | prev_top;  // lane 31's high cells, one slot up
+          prev_top = (t >> 30) & 3u;
+          if (lane == 0) lo_new = (w == 0) ? ((lo_lane0 & ~0xCu) | ((unsigned)bfresh << 2)) : lo_lane0;
+          Bw[w] = (Bw[w] << 16) | lo_new;
+          const unsigned x = ~(Aw[w] ^ Bw[w]);
+          MM[w] = (x | (x >> 1)) & 0x55555555u;  // bit 2k set: mismatch
+        }
+      }
+    }
+    // Rebase the packed scores when the best has run 4096 above the base.
+    if (best - rb >= kRebase) {
+      const int delta = best - rb;
+      const unsigned dn = pk_pair(-delta, -delta);
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
+        Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
+      }
+      rb = best;
+    }
+    const int thr_rel = best - rb - sc.X;
+    const unsigned nthr2 = pk_pair(-thr_rel, -thr_rel);
+    // Band test as int16 pairs: a = i - lo >= 0 and b = hi - i >= 0.
+    const int rel_lo = 2 * lane - (lo - 64 * cbase), rel_hi = (hi - 64 * cbase) - 2 * lane;
+    const unsigned A2 = pk_pair(rel_lo, rel_lo + 1), B2 = pk_pair(rel_hi, rel_hi - 1);
+    unsigned vmax2 = kNeg2, any_slots = 0;
+    int first = INT32_MAX, last = -1;
+#define DIBELLA_PK_I(S) ((S) < NC ? (S) : NC - 1)
+#define DIBELLA_PK_SLOT(S)                                                                         \
+  if (S < NC) {                                                                                    \
+    constexpr int s_ = DIBELLA_PK_I(S), p_ = s_ > 0 ? s_ - 1 : 0;                                  \
+    const unsigned prevH = __shfl_sync(kFull, top_lane ? H[p_] : H[s_], src_lane);                 \
+    const unsigned u2 = __byte_perm(H[s_], prevH, 0x1076u);                                        \
+    const unsigned bits = (MM[s_ >> 3] >> (2 * (s_ & 7))) & 0x00010001u;                           \
+    const unsigned sub2 = ((bits * 0xFFFFu) & S2) | (~(bits * 0xFFFFu) & M2);                      \
+    const unsigned ds = __viaddmax_s16x2(Up[s_], sub2, kNeg2);                                     \
+    unsigned h2 = __viaddmax_s16x2(__vmaxs2(u2, H[s_]), G2, ds);                                   \
+    const unsigned f = __vimin3_s16x2(__vadd2(h2, nthr2), __vadd2(A2, 0x00400040u * s_),          \
+                                      __vsub2(B2, 0x00400040u * s_));                              \
+    const unsigned dead = ((f >> 15) & 0x00010001u) * 0xFFFFu;                                     \
+    h2 = (h2 & ~dead) | (kNeg2 & dead);                                                            \
+    Up[s_] = u2;                                                                                   \
+    H[s_] = h2;                                                                                    \
+    vmax2 = __vmaxs2(vmax2, h2);                                                                   \
+    const unsigned blo_ = __ballot_sync(kFull, (h2 & 0xFFFFu) != 0xC000u);                         \
+    const unsigned bhi_ = __ballot_sync(kFull, (h2 >> 16) != 0xC000u);                             \
+    if (blo_ | bhi_) {                                                                             \
+      any_slots |= 1u << s_;                                                                       \
+      const int base_ = 64 * (cbase + s_);                                                         \
+      first = base_ + min(blo_ ? 2 * __ffs(blo_) - 2 : 64, bhi_ ? 2 * __ffs(bhi_) - 1 : 64);      \
+      if (last < 0) last = base_ + max(blo_ ? 62 - 2 * __clz(blo_) : -1, bhi_ ? 63 - 2 * __clz(bhi_) : -1); \
+    }                                                                                              \
+  }
+    switch (ntop) {
+      case 31: DIBELLA_PK_SLOT(31) [[fallthrough]];
+      case 30: DIBELLA_PK_SLOT(30) [[fallthrough]];
+      case 29: DIBELLA_PK_SLOT(29) [[fallthrough]];
+      case 28: DIBELLA_PK_SLOT(28) [[fallthrough]];
+      case 27: DIBELLA_PK_SLOT(27) [[fallthrough]];
+      case 26: DIBELLA_PK_SLOT(26) [[fallthrough]];
+      case 25: DIBELLA_PK_SLOT(25) [[fallthrough]];
+      case 24: DIBELLA_PK_SLOT(24) [[fallthrough]];
+      case 23: DIBELLA_PK_SLOT(23) [[fallthrough]];
+      case 22: DIBELLA_PK_SLOT(22) [[fallthrough]];
+      case 21: DIBELLA_PK_SLOT(21) [[fallthrough]];
+      case 20: DIBELLA_PK_SLOT(20) [[fallthrough]];
+      case 19: DIBELLA_PK_SLOT(19) [[fallthrough]];
+      case 18: DIBELLA_PK_SLOT(18) [[fallthrough]];
+      case 17: DIBELLA_PK_SLOT(17) [[fallthrough]];
+      case 16: DIBELLA_PK_SLOT(16) [[fallthrough]];
+      case 15: DIBELLA_PK_SLOT(15) [[fallthrough]];
+      case 14: DIBELLA_PK_SLOT(14) [[fallthrough]];
+      case 13: DIBELLA_PK_SLOT(13) [[fallthrough]];
+      case 12: DIBELLA_PK_SLOT(12) [[fallthrough]];
+      case 11: DIBELLA_PK_SLOT(11) [[fallthrough]];
+      case 10: DIBELLA_PK_SLOT(10) [[fallthrough]];
+      case 9: DIBELLA_PK_SLOT(9) [[fallthrough]];
+      case 8: DIBELLA_PK_SLOT(8) [[fallthrough]];
+      case 7: DIBELLA_PK_SLOT(7) [[fallthrough]];
+      case 6: DIBELLA_PK_SLOT(6) [[fallthrough]];
+      case 5: DIBELLA_PK_SLOT(5) [[fallthrough]];
+      case 4: DIBELLA_PK_SLOT(4) [[fallthrough]];
+      case 3: DIBELLA_PK_SLOT(3) [[fallthrough]];
+      case 2: DIBELLA_PK_SLOT(2) [[fallthrough]];
+      case 1: DIBELLA_PK_SLOT(1) [[fallthrough]];
+      default: break;
+    }
+#undef DIBELLA_PK_SLOT
+#undef DIBELLA_PK_I
+    H[0] = kNeg2;
+    cells += hi - lo + 1;
+    if (any_slots == 0) break;
+    const int vrel = __reduce_max_sync(kFull, max(pk_lo(vmax2), pk_hi(vmax2)));
+    const int sl = __ffs(any_slots) - 1, sh = 31 - __clz(any_slots);
+    if (vrel + rb > best) {
+      const unsigned v2 = pk_pair(vrel, vrel);
+      int cand = INT32_MAX;
+#pragma unroll
+      for (int s = 1; s < NC; ++s) {
+        if (s >= sl && s <= sh) {
+          const unsigned e = H[s] ^ v2;
+          const unsigned blo = __ballot_sync(kFull, (e & 0xFFFFu) == 0);
+          const unsigned bhi = __ballot_sync(kFull, (e >> 16) == 0);
+          const int f0 = blo ? 2 * (__ffs(blo) - 1) : INT32_MAX;
+          const int f1 = bhi ? 2 * (__ffs(bhi) - 1) + 1 : INT32_MAX;
+          if (min(f0, f1) != INT32_MAX) cand = min(cand, 64 * (cbase + s) + min(f0, f1));
+        }
+      }
+      best = vrel + rb;
       bi = cand;
       bj = d - cand;
     }
@@ -472,6 +712,29 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
     const int item = p.wide_q[q];
     const Item it = p.items[item];
     if (!extend_reg<NC>(p.words, it, p.sc, p.ext + item)) {
+      if (lane == 0) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        p.esc_q[s] = item;
+        atomicAdd(&p.cnt->stat[3], 1u);
+      }
+    } else if (lane == 0) {
+      atomicAdd(&p.cnt->cells[1], (unsigned long long)p.ext[item].cells);
+    }
+    __syncwarp();
+  }
+}
+
+// Packed form, one warp per extension (routed here only when X <= kPackedMaxX).
+template <int NC>
+__global__ void __launch_bounds__(kBlockThreads) wide_pk_kernel(ExtendParams p) {
+  const int lane = threadIdx.x & 31;
+  const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  for (;;) {
+    const unsigned q = pop_warp(p.cnt, p.wide_q_id);
+    if (q >= tail) break;
+    const int item = p.wide_q[q];
+    const Item it = p.items[item];
+    if (!extend_pk<NC>(p.words, it, p.sc, p.ext + item)) {
       if (lane == 0) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
         p.esc_q[s] = item;
@@ -799,14 +1062,15 @@ thread_local std::string g_last_error;
 std::mutex g_mu;
 dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/16, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/64,
-    /*wide_slots=*/16, /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0, /*n_buckets=*/6,
-    {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
+    /*wide_slots=*/0, /*wide_packed=*/1, /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0,
+    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
 
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
   int narrow_blocks[3] = {0, 0, 0};  // narrow_kernel<32/48/64> blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
+  int pk_blocks[3] = {0, 0, 0};      // wide_pk_kernel<16/24/32> blocks per SM
   int smem_blocks = 0;               // wide_smem_kernel blocks per SM
 };
 std::mutex g_dev_mu;
@@ -830,7 +1094,7 @@ int gband_cap_for(int32_t max_read_len) {
 }
 
 struct Layout {
-  size_t counters, items, ext, queue[4], gband, total;
+  size_t counters, items, ext, queue[kNumQ], gband, total;
 };
 
 Layout layout_for(long long n_pairs, int gcap) {
@@ -842,7 +1106,7 @@ Layout layout_for(long long n_pairs, int gcap) {
   off = align256(off + sizeof(Item) * 2 * (size_t)n_pairs);
   L.ext = off;
   off = align256(off + sizeof(ExtOut) * 2 * (size_t)n_pairs);
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kNumQ; ++q) {
     L.queue[q] = off;
     off = align256(off + sizeof(int) * 2 * (size_t)n_pairs);
   }
@@ -893,6 +1157,9 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.narrow_blocks[2], (const void*)narrow_kernel<64>, kBlockThreads, narrow_smem<64>())) ||
         (rc = occupancy(&D.reg_blocks[0], (const void*)wide_reg_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.reg_blocks[1], (const void*)wide_reg_kernel<32>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.pk_blocks[0], (const void*)wide_pk_kernel<16>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.pk_blocks[1], (const void*)wide_pk_kernel<24>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.pk_blocks[2], (const void*)wide_pk_kernel<32>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.smem_blocks, (const void*)wide_smem_kernel, kSmemWarps * 32, kWideSmemBytes)))
       return rc;
     D.ready = true;
@@ -903,7 +1170,8 @@ int device_info(DeviceInfo** out) {
 
 int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
-  if (s.wide_slots != 16 && s.wide_slots != 32) return DIBELLA_EINVAL;
+  if (s.wide_slots != 0 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32) return DIBELLA_EINVAL;
+  if (s.wide_packed != 0 && s.wide_packed != 1) return DIBELLA_EINVAL;
   if (s.n_buckets < 1 || s.n_buckets > DIBELLA_MAX_BUCKETS) return DIBELLA_EINVAL;
   if (s.wide_blocks_per_sm < 0 || s.narrow_blocks_per_sm < 0) return DIBELLA_EINVAL;
   for (int b = 1; b < s.n_buckets - 1; ++b)
@@ -951,53 +1219,78 @@ cudaError_t launch_narrow(int wt, int grid, cudaStream_t st, const ExtendParams&
   return cudaGetLastError();
 }
 
-cudaError_t launch_wide_reg(int slots, int grid, cudaStream_t st, const ExtendParams& ep) {
-  if (slots == 16)
+// The wide form of a schedule: packed int16 pairs when allowed, else int32.
+cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, cudaStream_t st,
+                        const ExtendParams& ep) {
+  dibella_schedule_t sch = sch_in;
+  if (sch.wide_slots == 0) sch.wide_slots = xdrop <= 30 ? 16 : 24;  // auto: band grows with X
+  const bool packed = sch.wide_packed && xdrop <= kPackedMaxX;
+  int b;
+  if (packed) {
+    const int vi = sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2);
+    b = D.pk_blocks[vi];
+  } else {
+    b = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
+  }
+  if (sch.wide_blocks_per_sm > 0) b = std::min(b, sch.wide_blocks_per_sm);
+  const int grid = D.sms * b;
+  if (packed) {
+    if (sch.wide_slots == 16)
+      wide_pk_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
+    else if (sch.wide_slots == 24)
+      wide_pk_kernel<24><<<grid, kBlockThreads, 0, st>>>(ep);
+    else
+      wide_pk_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+  } else if (sch.wide_slots == 16) {
     wide_reg_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
-  else
+  } else {
     wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+  }
   return cudaGetLastError();
 }
 
-// All extension launches of one batch: register form on the wide queue,
-// narrow form on the narrow queue (both escalate to Esc1), shared-memory
-// form on Esc1 (escalates to Esc2), global-band form on Esc2.
-int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, ExtendParams ep, int* const q[4],
-                      cudaStream_t st) {
+// All extension launches of one batch, in stream order:
+//   narrow form   on Narrow (outgrown -> Esc1)
+//   wide form     on Wide   (outgrown -> Esc2)
+//   wide form     on Esc1   (outgrown -> Esc2)
+//   shared-memory form on Esc2 (outgrown -> Esc3)
+//   global form   on Esc3
+int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, int xdrop, ExtendParams ep,
+                      int* const q[kNumQ], cudaStream_t st) {
   const int wt = sch.narrow_band_cap;
   const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
   int nb = D.narrow_blocks[vi];
   if (sch.narrow_blocks_per_sm > 0) nb = std::min(nb, sch.narrow_blocks_per_sm);
-  int rb = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
-  if (sch.wide_blocks_per_sm > 0) rb = std::min(rb, sch.wide_blocks_per_sm);
   cudaError_t e;
-
-  ep.wide_q = q[kQWide];
-  ep.wide_q_id = kQWide;
-  ep.narrow_q = nullptr;
-  ep.narrow_q_id = -1;
-  ep.esc_q = q[kQEsc1];
-  ep.esc_q_id = kQEsc1;
-  if ((e = launch_wide_reg(sch.wide_slots, D.sms * rb, st, ep)) != cudaSuccess)
-    return cuda_fail(e, "wide_reg launch");
-  record(st, 2);
 
   ep.wide_q = nullptr;
   ep.narrow_q = q[kQNarrow];
   ep.narrow_q_id = kQNarrow;
+  ep.esc_q = q[kQEsc1];
+  ep.esc_q_id = kQEsc1;
   if ((e = launch_narrow(wt, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
-  record(st, 3);
+  record(st, 2);
 
-  ep.wide_q = q[kQEsc1];
-  ep.wide_q_id = kQEsc1;
   ep.narrow_q = nullptr;
   ep.esc_q = q[kQEsc2];
   ep.esc_q_id = kQEsc2;
-  wide_smem_kernel<<<D.sms * D.smem_blocks, kSmemWarps * 32, kWideSmemBytes, st>>>(ep);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_smem launch");
+  ep.wide_q = q[kQWide];
+  ep.wide_q_id = kQWide;
+  if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
+  record(st, 3);
+  ep.wide_q = q[kQEsc1];
+  ep.wide_q_id = kQEsc1;
+  if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
 
   ep.wide_q = q[kQEsc2];
   ep.wide_q_id = kQEsc2;
+  ep.esc_q = q[kQEsc3];
+  ep.esc_q_id = kQEsc3;
+  wide_smem_kernel<<<D.sms * D.smem_blocks, kSmemWarps * 32, kWideSmemBytes, st>>>(ep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_smem launch");
+
+  ep.wide_q = q[kQEsc3];
+  ep.wide_q_id = kQEsc3;
   global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
   record(st, 4);
@@ -1122,9 +1415,9 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.sc = {scoring.match, scoring.mismatch, scoring.gap, scoring.xdrop};
   ep.gband = (int*)(ws + L.gband);
   ep.gcap = gcap;
-  int* q[4];
-  for (int i = 0; i < 4; ++i) q[i] = (int*)(ws + L.queue[i]);
-  rc = launch_extensions(*D, sch, ep, q, st);
+  int* q[kNumQ];
+  for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
+  rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
   if (rc != DIBELLA_OK) return rc;
   rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
   record(st, 5);
@@ -1169,6 +1462,54 @@ int dibella_xdrop_batch_host(const uint32_t* packed_words, const int64_t* read_w
   return DIBELLA_OK;
 }
 
+int dibella_xdrop_stream(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                         const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* host_pairs,
+                         int64_t n_pairs, int64_t chunk_pairs, int32_t k, dibella_scoring_t scoring,
+                         dibella_result_t* host_results, void* const* staging, void* const* workspace,
+                         int64_t workspace_bytes, void* const* streams, const dibella_schedule_t* sched,
+                         int64_t* n_chunks_out) {
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  if (chunk_pairs < 1 || chunk_pairs > (1ll << 29) || !staging || !workspace || !streams) return DIBELLA_EINVAL;
+  if (n_pairs > 0 && (!host_pairs || !host_results)) return DIBELLA_EINVAL;
+  for (int s = 0; s < 2; ++s)
+    if (!staging[s] || ((uintptr_t)staging[s] & 255) || !workspace[s]) return DIBELLA_EINVAL;
+  int64_t start = 0, chunks = 0;
+  while (start < n_pairs) {
+    int64_t end = std::min(n_pairs, start + chunk_pairs);
+    if (end < n_pairs) {  // never split the seed records of one candidate pair
+      int64_t e2 = end;
+      while (e2 > start && host_pairs[e2].read_a == host_pairs[e2 - 1].read_a &&
+             host_pairs[e2].read_b == host_pairs[e2 - 1].read_b)
+        --e2;
+      if (e2 == start) return DIBELLA_EINVAL;  // one candidate pair has more seeds than a chunk holds
+      end = e2;
+    }
+    const int slot = (int)(chunks & 1);
+    cudaStream_t st = (cudaStream_t)streams[slot];
+    const int64_t n = end - start;
+    dibella_pair_t* dpairs = (dibella_pair_t*)staging[slot];
+    dibella_result_t* dres =
+        (dibella_result_t*)((char*)staging[slot] + align256(sizeof(dibella_pair_t) * (size_t)chunk_pairs));
+    cudaError_t e = cudaMemcpyAsync(dpairs, host_pairs + start, sizeof(dibella_pair_t) * n,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+    rc = dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads, dpairs, n, k, scoring, dres,
+                             workspace[slot], workspace_bytes, streams[slot], sched);
+    if (rc != DIBELLA_OK) return rc;
+    e = cudaMemcpyAsync(host_results + start, dres, sizeof(dibella_result_t) * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+    start = end;
+    ++chunks;
+  }
+  for (int s = 0; s < 2; ++s) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)streams[s]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (n_chunks_out) *n_chunks_out = chunks;
+  return DIBELLA_OK;
+}
+
 int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_word_offsets,
                            const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
                            int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
@@ -1197,6 +1538,106 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "per-pair launch");
   return finish(read_lengths, pairs, n_pairs, k, results, (const ExtOut*)(ws + L.ext), st);
+}
+
+int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                     const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                     int64_t n_pairs, int32_t k, dibella_scoring_t scoring, dibella_result_t* results,
+                     void* workspace, int64_t workspace_bytes, void* stream, int32_t repeats,
+                     dibella_schedule_t* best_out, float* best_ms_out, int32_t* n_tried_out) {
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  if (!best_out || repeats < 1 || n_pairs < 1) return DIBELLA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return DIBELLA_EINVAL;  // timing needs a live stream
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  int tried = 0;
+  // Median of `repeats` timed runs (after one untimed run) of one schedule.
+  auto time_one = [&](const dibella_schedule_t& cand, float* ms_out) -> int {
+    float best = 0;
+    std::vector<float> t;
+    for (int r = 0; r <= repeats; ++r) {
+      cudaEventRecord(e0, st);
+      int rr = dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
+                                   scoring, results, workspace, workspace_bytes, stream, &cand);
+      if (rr != DIBELLA_OK) return rr;
+      cudaEventRecord(e1, st);
+      cudaError_t ee = cudaEventSynchronize(e1);
+      if (ee != cudaSuccess) return cuda_fail(ee, "cudaEventSynchronize");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    best = t[t.size() / 2];
+    *ms_out = best;
+    ++tried;
+    return DIBELLA_OK;
+  };
+  dibella_schedule_t cur;
+  dibella_get_default_schedule(&cur);
+  float cur_ms = 0;
+  rc = time_one(cur, &cur_ms);
+  auto consider = [&](const dibella_schedule_t& cand) -> int {
+    if (validate_schedule(cand) != DIBELLA_OK) return DIBELLA_OK;
+    float ms = 0;
+    int rr = time_one(cand, &ms);
+    if (rr != DIBELLA_OK) return rr;
+    if (ms < cur_ms) {
+      cur = cand;
+      cur_ms = ms;
+    }
+    return DIBELLA_OK;
+  };
+  // Stage 1: routing (thread- vs warp-per-extension) x per-thread band chunk.
+  const int lens[5] = {-1, 2000, 8000, 32000, 1 << 30};
+  const int caps[3] = {32, 48, 64};
+  const dibella_schedule_t base1 = cur;
+  for (int li = 0; li < 5 && rc == DIBELLA_OK; ++li)
+    for (int ci = 0; ci < 3 && rc == DIBELLA_OK; ++ci) {
+      dibella_schedule_t c = base1;
+      c.narrow_max_xdrop = lens[li] < 0 ? -1 : DIBELLA_XDROP_INF;
+      c.narrow_max_len = lens[li] < 0 ? 0 : lens[li];
+      c.narrow_band_cap = caps[ci];
+      if (li == 0 && ci > 0) continue;  // all-wide ignores the narrow chunk
+      rc = consider(c);
+    }
+  // Stage 2: register slots of the warp form.
+  for (int ws = 16; ws <= 32 && rc == DIBELLA_OK; ws += 8) {
+    dibella_schedule_t c = cur;
+    c.wide_slots = ws;
+    rc = consider(c);
+  }
+  // Stage 3: resident blocks per SM (occupancy maximum, or capped).
+  for (int b = 1; b <= 3 && rc == DIBELLA_OK; ++b) {
+    dibella_schedule_t c = cur;
+    c.wide_blocks_per_sm = b;
+    c.narrow_blocks_per_sm = b;
+    rc = consider(c);
+  }
+  // Stage 4: length buckets that order the queues (longest first).
+  const int sets[3][DIBELLA_MAX_BUCKETS + 1] = {
+      {2, 5000, 0, 0, 0, 0, 0, 0, 0},
+      {6, 500, 2000, 5000, 10000, 20000, 0, 0, 0},
+      {8, 300, 1000, 2500, 5000, 10000, 20000, 40000, 0}};
+  for (int si = 0; si < 3 && rc == DIBELLA_OK; ++si) {
+    dibella_schedule_t c = cur;
+    c.n_buckets = sets[si][0];
+    for (int b = 0; b < DIBELLA_MAX_BUCKETS; ++b) c.bucket_bounds[b] = sets[si][1 + b];
+    rc = consider(c);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DIBELLA_OK) return rc;
+  *best_out = cur;
+  if (best_ms_out) *best_ms_out = cur_ms;
+  if (n_tried_out) *n_tried_out = tried;
+  return DIBELLA_OK;
 }
 
 int dibella_enable_phase_timing(int enable) {

@@ -56,7 +56,7 @@ def test_pack_layout_round_trip():
     offs = np.cumsum([0] + [len(r) for r in reads]).astype(np.int64)
     words, woffs, lens = dib.dibella_pack_reads(ascii, offs, n_threads=3)
     assert words.dtype == np.uint32 and len(words) == dib.dibella_packed_words(offs)
-    assert list(words[:4]) == [0, 0, 0, 0] and list(words[-4:]) == [0, 0, 0, 0]
+    assert list(words[:8]) == [0] * 8 and list(words[-8:]) == [0] * 8
     comp = str.maketrans("ACGT", "TGCA")
     for r, s in enumerate(reads):
         s = s.upper()
@@ -94,7 +94,7 @@ def test_size_queries_validate():
 def test_schedule_validation():
     s = dib.dibella_get_default_schedule()
     d = s.as_dict()
-    assert d["narrow_band_cap"] in (32, 48, 64)
+    assert d["narrow_band_cap"] in (32, 48, 64) and d["wide_slots"] in (0, 16, 24, 32)
     bad = dib.Schedule.from_dict(dict(d, narrow_band_cap=40))
     with pytest.raises(dib.DibellaError):
         dib.dibella_set_default_schedule(bad)

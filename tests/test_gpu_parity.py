@@ -33,12 +33,15 @@ def test_c1_all_pairs(c1, X):
     assert ((got["status"] & 4) != 0).sum() == len(workloads.pair_groups(c1.pairs)) - 1
 
 
-@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "wide16", "wide32"])
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "packed16", "packed24", "packed32",
+                                  "int16", "int32"])
 @pytest.mark.parametrize("X", [0, 3, 7, 25])
 def test_every_kernel_form_matches(c1, form, X):
     """Route every extension to one form; escalations must reproduce the result."""
-    if form.startswith("wide"):
-        sched = schedule(wide_slots=int(form[4:]), **WIDE_ALL)
+    if form.startswith("packed"):
+        sched = schedule(wide_slots=int(form[6:]), wide_packed=1, **WIDE_ALL)
+    elif form.startswith("int"):
+        sched = schedule(wide_slots=int(form[3:]), wide_packed=0, **WIDE_ALL)
     else:
         sched = schedule(narrow_band_cap=int(form[6:]), **NARROW_ALL)
     pairs = c1.pairs[:300]
@@ -101,17 +104,19 @@ def test_fuzz_medium(scoring):
     for X in (0, 1, 5, 12, 40):
         sc = scoring + (X,)
         exp = oracle_align(ascii, offs, pairs, k, sc)
-        for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL)):
+        for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL),
+                      schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
             assert_same(got, exp, "scoring %s X=%d" % (sc, X))
 
 
-@pytest.mark.parametrize("lengths,counter", [((900, 1300), "escalated_register"),
+@pytest.mark.parametrize("lengths,counter", [((900, 1300), "escalated_wide"),
                                               ((4300, 4800), "escalated_smem")])
 def test_infinite_x_escalations(lengths, counter):
-    """X = infinity: the band is the whole matrix.  Extensions longer than the
-    register band (448 cells) in both reads go to the shared-memory form, and
-    longer than its 4096 cells to the global-memory form."""
+    """X = infinity: the band is the whole matrix (and X is above the packed
+    form's limit, so the int32 register form runs).  Extensions wider than its
+    band go to the shared-memory form, and wider than 4096 cells to the
+    global-memory form."""
     import paper_2001_10049_gb300 as dib
     rng = random.Random(lengths[0])
     reads = random_overlap_reads(rng, 5, lengths[0], lengths[1], 0.1)
@@ -221,3 +226,16 @@ def test_c2_full_size_sampled():
         g = workloads.pair_groups(w.pairs)
         assert ((got["status"] & 4) != 0).sum() == len(g) - 1
         assert ((got["status"] & 8) != 0).sum() == 0
+
+
+@pytest.mark.parametrize("scoring,X", [((20, -20, -20), 150), ((64, -30, -64), 500), ((64, -64, -64), 8000),
+                                       ((64, -64, -64), 8001)])
+def test_packed_form_large_scores(c1, scoring, X):
+    """Scores far above the int16 range: the packed form rebases its 16-bit
+    cells as the best grows (X <= 8000), and X = 8001 takes the int32 form."""
+    pairs = c1.pairs[:150]
+    sc = scoring + (X,)
+    exp = oracle_align(c1.reads, c1.offsets, pairs, 17, sc)
+    for slots in (16, 24):
+        got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, sched=schedule(wide_slots=slots, **WIDE_ALL))
+        assert_same(got, exp, "scoring %s X=%d slots=%d" % (scoring, X, slots))
