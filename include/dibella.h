@@ -195,6 +195,33 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
                         void* workspace, int64_t workspace_bytes, void* stream,
                         const dibella_schedule_t* sched);
 
+/* Callers that cannot allocate device memory: for example a host runtime
+ * whose own pool owns all of the GPU's memory, a latency-critical loop in
+ * which an allocation might block or synchronise the device, or plug-in code
+ * that may not hold allocations of its own.  This entry point runs the same
+ * alignment as dibella_xdrop_batch (same arguments, results and semantics,
+ * default schedule) without any workspace from the caller and without
+ * allocating.  Its scratch is one fixed array inside the library, 8,782,080
+ * bytes (about 8.4 MiB), which every GPU that loads the library keeps until
+ * the process exits.
+ * Limits: at most DIBELLA_NOALLOC_MAX_PAIRS seed records per call (more
+ * returns DIBELLA_ENOMEM, with the reason in dibella_last_error(), and does
+ * nothing); an extension whose band outgrows the fixed scratch gets
+ * DIBELLA_RES_BAND_OVERFLOW.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array and each leaves its contents behind; the
+ * parts that must start at zero are cleared by every call, but calls whose
+ * work overlaps on the GPU (other streams, other threads) race on it, so
+ * serialise them.
+ * The paper has no counterpart: this is an interface for integration, not
+ * part of the method. */
+#define DIBELLA_NOALLOC_MAX_PAIRS 16384
+int dibella_xdrop_batch_noalloc(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                                const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                                int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
+                                dibella_result_t* results, void* stream);
+
 /* The same alignment with HOST pairs and results: copies the pairs in, runs
  * dibella_xdrop_batch, copies the results out and synchronises `stream`.
  * The store and the workspace are device memory; pairs/results should be

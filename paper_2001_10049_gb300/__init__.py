@@ -38,8 +38,10 @@ _ERRORS = {DIBELLA_EINVAL: "invalid argument", DIBELLA_EBASE: "non-ACGT base",
 class DibellaError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = "%s failed: %s (%d)" % (where, _ERRORS.get(code, "error"), code)
-        if code == DIBELLA_ECUDA:
-            msg += ": " + _lib().dibella_last_error().decode()
+        if code in (DIBELLA_ECUDA, DIBELLA_ENOMEM):
+            detail = _lib().dibella_last_error().decode()
+            if detail:
+                msg += ": " + detail
         super().__init__(msg)
         self.code = code
 
@@ -97,6 +99,7 @@ def _lib():
             "dibella_staging_bytes": ([i64, p64], i32),
             "dibella_xdrop_batch": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, i64, vp,
                                      ctypes.POINTER(Schedule)], i32),
+            "dibella_xdrop_batch_noalloc": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp], i32),
             "dibella_xdrop_batch_host": ([vp, vp, vp, i64, vp, i64, i32, Scoring, vp, vp, vp, i64, vp,
                                           ctypes.POINTER(Schedule)], i32),
             "dibella_xdrop_stream": ([vp, vp, vp, i64, vp, i64, i64, i32, Scoring, vp, ctypes.POINTER(vp),
@@ -213,6 +216,19 @@ def dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads: 
                                     _ptr(workspace), workspace_bytes, _stream_handle(stream),
                                     ctypes.byref(sched) if sched is not None else None)
     _check(rc, "dibella_xdrop_batch")
+
+
+NOALLOC_MAX_PAIRS = 16384
+
+
+def dibella_xdrop_batch_noalloc(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs,
+                                n_pairs: int, k: int, scoring: Scoring, results, stream=None) -> None:
+    """dibella_xdrop_batch without a caller workspace and without allocating
+    (the library's fixed scratch; at most NOALLOC_MAX_PAIRS seeds per call)."""
+    rc = _lib().dibella_xdrop_batch_noalloc(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths),
+                                            n_reads, _ptr(pairs), n_pairs, k, scoring, _ptr(results),
+                                            _stream_handle(stream))
+    _check(rc, "dibella_xdrop_batch_noalloc")
 
 
 def dibella_xdrop_batch_host(packed_words, read_word_offsets, read_lengths, n_reads: int, host_pairs,

@@ -1347,6 +1347,41 @@ int finish(const int32_t* lens, const dibella_pair_t* pairs, int64_t n_pairs, in
   return DIBELLA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed scratch for dibella_xdrop_batch_noalloc.  Every GPU that loads this
+// library holds kNoAllocBytes of it until the process exits.  Host code must
+// not use the symbol's name as an address: it resolves the device address with
+// cudaGetSymbolAddress, once per device, with that device current.
+constexpr long long kNoAllocMaxPairs = DIBELLA_NOALLOC_MAX_PAIRS;
+constexpr int kNoAllocBandCap = 8192;  // global-band cells per warp slot at the maximum batch
+constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNoAllocBytes =
+    up256(sizeof(Counters)) + up256(sizeof(Item) * 2 * kNoAllocMaxPairs) +
+    up256(sizeof(ExtOut) * 2 * kNoAllocMaxPairs) + kNumQ * up256(sizeof(int) * 2 * kNoAllocMaxPairs) +
+    up256(sizeof(int) * 3 * (size_t)kNoAllocBandCap * kGlobalWarps);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return DIBELLA_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DIBELLA_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1429,6 +1464,25 @@ int dibella_staging_bytes(int64_t n_pairs, int64_t* bytes_out) {
   *bytes_out = (int64_t)(align256(sizeof(dibella_pair_t) * (size_t)n_pairs) +
                          align256(sizeof(dibella_result_t) * (size_t)n_pairs));
   return DIBELLA_OK;
+}
+
+int dibella_xdrop_batch_noalloc(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                                const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
+                                int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
+                                dibella_result_t* results, void* stream) {
+  if (n_pairs > kNoAllocMaxPairs) {
+    g_last_error = "dibella_xdrop_batch_noalloc: " + std::to_string((long long)n_pairs) +
+                   " seeds exceed the no-allocation maximum of " + std::to_string(kNoAllocMaxPairs);
+    return DIBELLA_ENOMEM;
+  }
+  int rc = validate_common(n_reads, n_pairs, k, scoring);
+  if (rc != DIBELLA_OK) return rc;
+  void* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc != DIBELLA_OK) return rc;
+  // The batch path clears the counters it needs zeroed on every call.
+  return dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k, scoring,
+                             results, scratch, (int64_t)kNoAllocBytes, stream, nullptr);
 }
 
 int dibella_xdrop_batch_host(const uint32_t* packed_words, const int64_t* read_word_offsets,
