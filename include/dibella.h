@@ -120,16 +120,20 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  * on the schedule; only speed does.  Every extension first goes to one of:
  *   narrow  one thread per extension, band in per-thread shared memory of
  *           narrow_band_cap cells (32, 48 or 64);
- *   wide    one warp per extension, band in registers: wide_slots chunks
- *           (16, 24 or 32), of which wide_slots - 2 hold the band; a chunk
- *           is 64 cells packed as int16 pairs when wide_packed is set and
+ *   wide    a warp (or a group of 16 or 8 lanes) per extension, band in
+ *           registers: wide_slots chunks (16, 24 or 32), of which
+ *           wide_slots - 2 hold the band; a chunk is 2 cells per lane
+ *           packed as int16 pairs when wide_packed is set and
  *           xdrop <= 8000 (exact: scores are kept relative to a moving base),
- *           else 32 int32 cells;
+ *           else 32 int32 cells of one warp;
  * an extension whose band outgrows its form is re-run from the start by a
  * warp with a 4096-cell shared-memory band, and beyond that by a warp whose
  * band lives in the workspace (sized by max_read_len: it cannot overflow).
  * An extension is routed to narrow when xdrop <= narrow_max_xdrop and
- * min(remaining A, remaining B) <= narrow_max_len.  Work is ordered by
+ * min(remaining A, remaining B) <= narrow_max_len.  When a call passes no
+ * schedule, batches with fewer than 4 extensions per resident narrow lane go
+ * entirely to the wide form (they would wait on one lane's longest
+ * extension); an explicit schedule is followed as given.  Work is ordered by
  * n_buckets length buckets (longest first); bucket b holds keys below
  * bucket_bounds[b] (ascending), the last bucket everything else. */
 #define DIBELLA_MAX_BUCKETS 8
@@ -140,6 +144,9 @@ typedef struct {
   int32_t wide_slots;             /* 16, 24, 32, or 0 = 16 if xdrop <= 30     */
                                   /* else 24                                  */
   int32_t wide_packed;            /* 1: int16-pair cells when xdrop <= 8000   */
+  int32_t wide_group_lanes;       /* packed wide form: lanes per extension,   */
+                                  /* 32 (one warp), 16 or 8 (2 or 4 per warp, */
+                                  /* chunks of 2 cells per lane); 0 = 32      */
   int32_t wide_blocks_per_sm;     /* 0 = occupancy maximum                   */
   int32_t narrow_blocks_per_sm;   /* 0 = occupancy maximum                   */
   int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
@@ -268,9 +275,10 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
  * given (sample) batch with candidate schedules and returns the fastest in
  * *best_out (median of `repeats` timed runs each, CUDA events on `stream`).
  * The search is staged: routing threshold between the one-thread and the
- * one-warp forms x per-thread band chunk (32/48/64), then register slots of
- * the warp form (16/32), then resident blocks per SM, then length-bucket
- * bounds; each stage keeps the best so far.  Same arguments as
+ * wide forms x per-thread band chunk (32/48/64), then lanes per extension
+ * (32/16/8) x register slots (16/24/32) of the wide form, then resident
+ * blocks per SM, then length-bucket bounds; each stage keeps the best so
+ * far.  Same arguments as
  * dibella_xdrop_batch; results hold the last run's output.  Synchronises
  * `stream`; refused (EINVAL) while `stream` is capturing.  *best_ms_out and
  * *n_tried_out (either may be NULL) receive the winner's time and the number

@@ -54,14 +54,16 @@ class Scoring(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("narrow_max_xdrop", ctypes.c_int32), ("narrow_max_len", ctypes.c_int32),
                 ("narrow_band_cap", ctypes.c_int32), ("wide_slots", ctypes.c_int32),
-                ("wide_packed", ctypes.c_int32), ("wide_blocks_per_sm", ctypes.c_int32),
+                ("wide_packed", ctypes.c_int32), ("wide_group_lanes", ctypes.c_int32),
+                ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
                 ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
                 "narrow_band_cap": self.narrow_band_cap, "wide_slots": self.wide_slots,
-                "wide_packed": self.wide_packed, "wide_blocks_per_sm": self.wide_blocks_per_sm,
+                "wide_packed": self.wide_packed, "wide_group_lanes": self.wide_group_lanes,
+                "wide_blocks_per_sm": self.wide_blocks_per_sm,
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
                 "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)]}
 
@@ -69,7 +71,7 @@ class Schedule(ctypes.Structure):
     def from_dict(cls, d: dict) -> "Schedule":
         s = cls()
         for key in ("narrow_max_xdrop", "narrow_max_len", "narrow_band_cap", "wide_slots", "wide_packed",
-                    "wide_blocks_per_sm",
+                    "wide_group_lanes", "wide_blocks_per_sm",
                     "narrow_blocks_per_sm", "n_buckets"):
             setattr(s, key, int(d[key]))
         bounds = list(d.get("bucket_bounds", []))

@@ -747,6 +747,316 @@ __global__ void __launch_bounds__(kBlockThreads) wide_pk_kernel(ExtendParams p) 
   }
 }
 
+// Grouped packed form: a warp runs 32/GL extensions at once, GL lanes each,
+// chunks of 2*GL cells (same cell encoding, slots, guard and base words as the
+// packed form).  Every per-extension scalar lives in the lanes of its group, so
+// the per-antidiagonal control is computed once for all groups of the warp.
+// Slot updates are predicated per group, the jump table enters at the highest
+// slot any group needs, and the rare divergent steps (shift, activation,
+// rebase, argmax) run under a warp vote with per-group predicates.  Each group
+// pops its next extension as soon as its current one ends.
+template <int GL, int NC>
+__global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p) {
+  static_assert(GL == 8 || GL == 16, "group of 8 or 16 lanes");
+  static_assert(NC % 8 == 0 && NC >= 8 && NC <= 32, "slots come in words of 8");
+  constexpr int NW = NC / 8;
+  constexpr int CH = 2 * GL;                 // cells per chunk
+  constexpr int LOG_CH = GL == 8 ? 4 : 5;
+  constexpr unsigned LOWMASK = (1u << GL) - 1u;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / GL, gl = lane % GL;
+  const unsigned gmask = LOWMASK << (GL * g);
+  const int src = (gl + GL - 1) & (GL - 1);
+  const bool top = gl == GL - 1;
+  const Scoring sc = p.sc;
+  const unsigned M2 = pk_pair(sc.M, sc.M), S2 = pk_pair(sc.S, sc.S), G2 = pk_pair(sc.G, sc.G);
+  const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  const uint32_t* __restrict__ words = p.words;
+
+  bool active = false, exhausted = false;
+  int item = 0, m = 0, n = 0, d = 0, live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  int cbase = 0, ctop = 0, rb = 0;
+  long long a_lo = 0, b_lo = 0, cells = 0;
+  unsigned H[NC], Up[NC], Aw[NW], Bw[NW];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    H[s] = kNeg2;
+    Up[s] = kNeg2;
+  }
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    Aw[w] = 0;
+    Bw[w] = 0;
+  }
+
+  for (;;) {
+    // Refill: every group without work pops one extension.
+    const bool want = !active && !exhausted;
+    if (__any_sync(kFull, want)) {
+      unsigned q = 0;
+      if (want && gl == 0) q = atomicAdd(&p.cnt->head[p.wide_q_id], 1u);
+      q = __shfl_sync(kFull, q, lane & ~(GL - 1));
+      if (want) {
+        if (q < tail) {
+          item = p.wide_q[q];
+          const Item it = p.items[item];
+          m = it.m;
+          n = it.n;
+          a_lo = it.a0 - 1;
+          b_lo = it.b0 + 1;
+#pragma unroll
+          for (int s = 0; s < NC; ++s) {
+            H[s] = kNeg2;
+            Up[s] = kNeg2;
+          }
+          if (gl == 0) H[1] = pk_pair(0, -16384);
+          const int i0 = 2 * gl;
+          Aw[0] = ((unsigned)base_of(words, a_lo + i0) << 2) | ((unsigned)base_of(words, a_lo + i0 + 1) << 18);
+          Bw[0] = ((unsigned)base_of(words, b_lo + i0) << 2) | ((unsigned)base_of(words, b_lo + i0 + 1) << 18);
+#pragma unroll
+          for (int w = 1; w < NW; ++w) {
+            Aw[w] = 0;
+            Bw[w] = 0;
+          }
+          cbase = -1;
+          ctop = 0;
+          rb = 0;
+          d = 1;
+          live_lo = live_hi = 0;
+          best = bi = bj = 0;
+          cells = 0;
+          active = true;
+          if (m + n == 0) {
+            if (gl == 0) {
+              ExtOut o;
+              o.best = 0; o.i_end = 0; o.j_end = 0; o.status = 0; o.cells = 0;
+              p.ext[item] = o;
+            }
+            active = false;
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) {
+      if (__all_sync(kFull, exhausted)) break;
+      continue;
+    }
+
+    // One antidiagonal for every active group.
+    int lo = 0, hi = -1, c0 = 0;
+    if (active) {
+      lo = max(live_lo, d - n);
+      hi = min(min(live_hi + 1, d), m);
+      c0 = lo >> LOG_CH;
+    }
+    for (;;) {  // keep slot 0 = chunk c0 - 1
+      const bool need = active && cbase < c0 - 1;
+      if (!__any_sync(kFull, need)) break;
+      if (need) {
+#pragma unroll
+        for (int s = 0; s + 1 < NC; ++s) {
+          H[s] = H[s + 1];
+          Up[s] = Up[s + 1];
+        }
+        H[NC - 1] = kNeg2;
+        Up[NC - 1] = kNeg2;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int wn = w + 1 < NW ? w + 1 : w;
+          const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
+          Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
+          Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
+        }
+        ++cbase;
+      }
+    }
+    const int cneed = (hi + 1) >> LOG_CH;
+    if (active && cneed - cbase > NC - 1) {  // band outgrew the slots: hand over
+      if (gl == 0) {
+        const unsigned s2 = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        p.esc_q[s2] = item;
+        atomicAdd(&p.cnt->stat[3], 1u);
+      }
+      active = false;
+    }
+    const bool act_new = active && cneed > ctop;
+    if (__any_sync(kFull, act_new)) {
+      if (act_new) {
+        const int snew = cneed - cbase;
+        const int i0 = CH * cneed + 2 * gl;
+        const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
+        const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
+        const int sh = 2 * (snew & 7);
+        const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          if (w == (snew >> 3)) {
+            Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
+            Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+          }
+        }
+#pragma unroll
+        for (int s = 1; s < NC; ++s) {
+          if (s == snew) {
+            H[s] = kNeg2;
+            Up[s] = kNeg2;
+          }
+        }
+      }
+    }
+    if (active) ctop = cneed;
+    const int ntop = active ? ctop - cbase : 0;
+    const int ntop_w = __reduce_max_sync(kFull, ntop);
+    const int wtop_w = ntop_w >> 3;
+    unsigned MM[NW];
+    {
+      int bfresh = 0;
+      if (active) bfresh = base_of(words, b_lo - d + CH * c0);  // lane 0 of the group, low cell of slot 1
+      unsigned prev_top = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        MM[w] = 0;
+        if (w <= wtop_w) {
+          const unsigned t = __shfl_sync(kFull, Bw[w], src, GL);
+          unsigned lo_new = t >> 16;
+          const unsigned lo_lane0 = ((t >> 14) & 0xFFFCu) | prev_top;
+          prev_top = (t >> 30) & 3u;
+          if (gl == 0) lo_new = (w == 0) ? ((lo_lane0 & ~0xCu) | ((unsigned)bfresh << 2)) : lo_lane0;
+          Bw[w] = (Bw[w] << 16) | lo_new;
+          const unsigned x = ~(Aw[w] ^ Bw[w]);
+          MM[w] = (x | (x >> 1)) & 0x55555555u;
+        }
+      }
+    }
+    const bool reb = active && best - rb >= kRebase;
+    if (__any_sync(kFull, reb)) {
+      if (reb) {
+        const int delta = best - rb;
+        const unsigned dn = pk_pair(-delta, -delta);
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
+          Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
+        }
+        rb = best;
+      }
+    }
+    const int thr_rel = best - rb - sc.X;
+    const unsigned nthr2 = pk_pair(-thr_rel, -thr_rel);
+    const int rel_lo = 2 * gl - (lo - CH * cbase), rel_hi = (hi - CH * cbase) - 2 * gl;
+    const unsigned A2 = pk_pair(rel_lo, rel_lo + 1), B2 = pk_pair(rel_hi, rel_hi - 1);
+    unsigned vmax2 = kNeg2, any_slots = 0;
+    int first = INT32_MAX, last = -1;
+#define DIBELLA_GRP_I(S) ((S) < NC ? (S) : NC - 1)
+#define DIBELLA_GRP_SLOT(S)                                                                        \
+  if (S < NC) {                                                                                    \
+    constexpr int s_ = DIBELLA_GRP_I(S), p_ = s_ > 0 ? s_ - 1 : 0;                                 \
+    const bool act_ = s_ <= ntop;                                                                  \
+    const unsigned prevH = __shfl_sync(kFull, top ? H[p_] : H[s_], src, GL);                       \
+    const unsigned u2 = __byte_perm(H[s_], prevH, 0x1076u);                                        \
+    const unsigned bits = (MM[s_ >> 3] >> (2 * (s_ & 7))) & 0x00010001u;                           \
+    const unsigned sub2 = ((bits * 0xFFFFu) & S2) | (~(bits * 0xFFFFu) & M2);                      \
+    const unsigned ds = __viaddmax_s16x2(Up[s_], sub2, kNeg2);                                     \
+    unsigned h2 = __viaddmax_s16x2(__vmaxs2(u2, H[s_]), G2, ds);                                   \
+    const unsigned f = __vimin3_s16x2(__vadd2(h2, nthr2), __vadd2(A2, (unsigned)(CH * 0x00010001u) * s_), \
+                                      __vsub2(B2, (unsigned)(CH * 0x00010001u) * s_));             \
+    const unsigned dead = ((f >> 15) & 0x00010001u) * 0xFFFFu;                                     \
+    h2 = (h2 & ~dead) | (kNeg2 & dead);                                                            \
+    if (act_) {                                                                                    \
+      Up[s_] = u2;                                                                                 \
+      H[s_] = h2;                                                                                  \
+      vmax2 = __vmaxs2(vmax2, h2);                                                                 \
+    }                                                                                              \
+    const unsigned blo_ = (__ballot_sync(kFull, act_ && (h2 & 0xFFFFu) != 0xC000u) >> (GL * g)) & LOWMASK; \
+    const unsigned bhi_ = (__ballot_sync(kFull, act_ && (h2 >> 16) != 0xC000u) >> (GL * g)) & LOWMASK;     \
+    if (blo_ | bhi_) {                                                                             \
+      any_slots |= 1u << s_;                                                                       \
+      const int base_ = CH * (cbase + s_);                                                         \
+      first = base_ + min(blo_ ? 2 * __ffs(blo_) - 2 : CH, bhi_ ? 2 * __ffs(bhi_) - 1 : CH);      \
+      if (last < 0) last = base_ + max(blo_ ? 2 * (31 - __clz(blo_)) : -1, bhi_ ? 2 * (31 - __clz(bhi_)) + 1 : -1); \
+    }                                                                                              \
+  }
+    switch (ntop_w) {
+      case 31: DIBELLA_GRP_SLOT(31) [[fallthrough]];
+      case 30: DIBELLA_GRP_SLOT(30) [[fallthrough]];
+      case 29: DIBELLA_GRP_SLOT(29) [[fallthrough]];
+      case 28: DIBELLA_GRP_SLOT(28) [[fallthrough]];
+      case 27: DIBELLA_GRP_SLOT(27) [[fallthrough]];
+      case 26: DIBELLA_GRP_SLOT(26) [[fallthrough]];
+      case 25: DIBELLA_GRP_SLOT(25) [[fallthrough]];
+      case 24: DIBELLA_GRP_SLOT(24) [[fallthrough]];
+      case 23: DIBELLA_GRP_SLOT(23) [[fallthrough]];
+      case 22: DIBELLA_GRP_SLOT(22) [[fallthrough]];
+      case 21: DIBELLA_GRP_SLOT(21) [[fallthrough]];
+      case 20: DIBELLA_GRP_SLOT(20) [[fallthrough]];
+      case 19: DIBELLA_GRP_SLOT(19) [[fallthrough]];
+      case 18: DIBELLA_GRP_SLOT(18) [[fallthrough]];
+      case 17: DIBELLA_GRP_SLOT(17) [[fallthrough]];
+      case 16: DIBELLA_GRP_SLOT(16) [[fallthrough]];
+      case 15: DIBELLA_GRP_SLOT(15) [[fallthrough]];
+      case 14: DIBELLA_GRP_SLOT(14) [[fallthrough]];
+      case 13: DIBELLA_GRP_SLOT(13) [[fallthrough]];
+      case 12: DIBELLA_GRP_SLOT(12) [[fallthrough]];
+      case 11: DIBELLA_GRP_SLOT(11) [[fallthrough]];
+      case 10: DIBELLA_GRP_SLOT(10) [[fallthrough]];
+      case 9: DIBELLA_GRP_SLOT(9) [[fallthrough]];
+      case 8: DIBELLA_GRP_SLOT(8) [[fallthrough]];
+      case 7: DIBELLA_GRP_SLOT(7) [[fallthrough]];
+      case 6: DIBELLA_GRP_SLOT(6) [[fallthrough]];
+      case 5: DIBELLA_GRP_SLOT(5) [[fallthrough]];
+      case 4: DIBELLA_GRP_SLOT(4) [[fallthrough]];
+      case 3: DIBELLA_GRP_SLOT(3) [[fallthrough]];
+      case 2: DIBELLA_GRP_SLOT(2) [[fallthrough]];
+      case 1: DIBELLA_GRP_SLOT(1) [[fallthrough]];
+      default: break;
+    }
+#undef DIBELLA_GRP_SLOT
+#undef DIBELLA_GRP_I
+    H[0] = kNeg2;
+    if (active) cells += hi - lo + 1;
+    const int vrel = __reduce_max_sync(gmask, max(pk_lo(vmax2), pk_hi(vmax2)));
+    const bool improved = active && any_slots != 0 && vrel + rb > best;
+    if (__any_sync(kFull, improved)) {
+      const int sl = any_slots ? __ffs(any_slots) - 1 : NC, sh = any_slots ? 31 - __clz(any_slots) : 0;
+      const int sh_w = __reduce_max_sync(kFull, improved ? sh : 0);
+      const unsigned v2 = pk_pair(vrel, vrel);
+      int cand = INT32_MAX;
+#pragma unroll
+      for (int s = 1; s < NC; ++s) {
+        if (s > sh_w) break;
+        const bool in = improved && s >= sl && s <= sh;
+        const unsigned e = H[s] ^ v2;
+        const unsigned blo = (__ballot_sync(kFull, in && (e & 0xFFFFu) == 0) >> (GL * g)) & LOWMASK;
+        const unsigned bhi = (__ballot_sync(kFull, in && (e >> 16) == 0) >> (GL * g)) & LOWMASK;
+        const int f0 = blo ? 2 * (__ffs(blo) - 1) : INT32_MAX;
+        const int f1 = bhi ? 2 * (__ffs(bhi) - 1) + 1 : INT32_MAX;
+        if (min(f0, f1) != INT32_MAX) cand = min(cand, CH * (cbase + s) + min(f0, f1));
+      }
+      if (improved) {
+        best = vrel + rb;
+        bi = cand;
+        bj = d - cand;
+      }
+    }
+    const bool finished = active && (any_slots == 0 || d == m + n);
+    if (finished) {
+      if (gl == 0) {
+        ExtOut o;
+        o.best = best; o.i_end = bi; o.j_end = bj; o.status = 0; o.cells = cells;
+        p.ext[item] = o;
+        atomicAdd(&p.cnt->cells[1], (unsigned long long)cells);
+      }
+      active = false;
+    } else if (active) {
+      live_lo = first;
+      live_hi = last;
+      ++d;
+    }
+  }
+}
+
 // Shared-memory form, one warp per extension, band of kSmemCap cells.
 constexpr int kSmemCap = 4096;
 constexpr int kSmemWarps = 2;
@@ -1062,7 +1372,8 @@ thread_local std::string g_last_error;
 std::mutex g_mu;
 dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/16, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/64,
-    /*wide_slots=*/0, /*wide_packed=*/1, /*wide_blocks_per_sm=*/0, /*narrow_blocks_per_sm=*/0,
+    /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
+    /*narrow_blocks_per_sm=*/0,
     /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
 
 struct DeviceInfo {
@@ -1071,6 +1382,8 @@ struct DeviceInfo {
   int narrow_blocks[3] = {0, 0, 0};  // narrow_kernel<32/48/64> blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
   int pk_blocks[3] = {0, 0, 0};      // wide_pk_kernel<16/24/32> blocks per SM
+  int grp16_blocks[3] = {0, 0, 0};   // wide_grp_kernel<16, 16/24/32> blocks per SM
+  int grp8_blocks[2] = {0, 0};       // wide_grp_kernel<8, 16/24> blocks per SM
   int smem_blocks = 0;               // wide_smem_kernel blocks per SM
 };
 std::mutex g_dev_mu;
@@ -1160,6 +1473,11 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.pk_blocks[0], (const void*)wide_pk_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[1], (const void*)wide_pk_kernel<24>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[2], (const void*)wide_pk_kernel<32>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.grp16_blocks[0], (const void*)wide_grp_kernel<16, 16>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.grp16_blocks[1], (const void*)wide_grp_kernel<16, 24>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.grp16_blocks[2], (const void*)wide_grp_kernel<16, 32>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.grp8_blocks[0], (const void*)wide_grp_kernel<8, 16>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.grp8_blocks[1], (const void*)wide_grp_kernel<8, 24>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.smem_blocks, (const void*)wide_smem_kernel, kSmemWarps * 32, kWideSmemBytes)))
       return rc;
     D.ready = true;
@@ -1172,6 +1490,9 @@ int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
   if (s.wide_slots != 0 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32) return DIBELLA_EINVAL;
   if (s.wide_packed != 0 && s.wide_packed != 1) return DIBELLA_EINVAL;
+  if (s.wide_group_lanes != 0 && s.wide_group_lanes != 8 && s.wide_group_lanes != 16 && s.wide_group_lanes != 32)
+    return DIBELLA_EINVAL;
+  if (s.wide_group_lanes == 8 && s.wide_slots == 32) return DIBELLA_EINVAL;
   if (s.n_buckets < 1 || s.n_buckets > DIBELLA_MAX_BUCKETS) return DIBELLA_EINVAL;
   if (s.wide_blocks_per_sm < 0 || s.narrow_blocks_per_sm < 0) return DIBELLA_EINVAL;
   for (int b = 1; b < s.n_buckets - 1; ++b)
@@ -1223,28 +1544,48 @@ cudaError_t launch_narrow(int wt, int grid, cudaStream_t st, const ExtendParams&
 cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, cudaStream_t st,
                         const ExtendParams& ep) {
   dibella_schedule_t sch = sch_in;
-  if (sch.wide_slots == 0) sch.wide_slots = xdrop <= 30 ? 16 : 24;  // auto: band grows with X
   const bool packed = sch.wide_packed && xdrop <= kPackedMaxX;
+  int lanes = sch.wide_group_lanes;
+  if (lanes == 0) lanes = 32;  // auto: one warp per extension (measured fastest at X = 7..50)
+  if (!packed) lanes = 32;                                      // the int32 form is one warp per extension
+  if (sch.wide_slots == 0) sch.wide_slots = (lanes == 32) ? (xdrop <= 30 ? 16 : 24) : (xdrop <= 30 ? 16 : 24);
+  if (lanes == 8 && sch.wide_slots == 32) sch.wide_slots = 24;
+  const int vi = sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2);
   int b;
-  if (packed) {
-    const int vi = sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2);
-    b = D.pk_blocks[vi];
-  } else {
+  if (!packed)
     b = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
-  }
+  else if (lanes == 32)
+    b = D.pk_blocks[vi];
+  else if (lanes == 16)
+    b = D.grp16_blocks[vi];
+  else
+    b = D.grp8_blocks[vi];
   if (sch.wide_blocks_per_sm > 0) b = std::min(b, sch.wide_blocks_per_sm);
   const int grid = D.sms * b;
-  if (packed) {
+  if (!packed) {
     if (sch.wide_slots == 16)
+      wide_reg_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
+    else
+      wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+  } else if (lanes == 32) {
+    if (vi == 0)
       wide_pk_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
-    else if (sch.wide_slots == 24)
+    else if (vi == 1)
       wide_pk_kernel<24><<<grid, kBlockThreads, 0, st>>>(ep);
     else
       wide_pk_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
-  } else if (sch.wide_slots == 16) {
-    wide_reg_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
+  } else if (lanes == 16) {
+    if (vi == 0)
+      wide_grp_kernel<16, 16><<<grid, kBlockThreads, 0, st>>>(ep);
+    else if (vi == 1)
+      wide_grp_kernel<16, 24><<<grid, kBlockThreads, 0, st>>>(ep);
+    else
+      wide_grp_kernel<16, 32><<<grid, kBlockThreads, 0, st>>>(ep);
   } else {
-    wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+    if (vi == 0)
+      wide_grp_kernel<8, 16><<<grid, kBlockThreads, 0, st>>>(ep);
+    else
+      wide_grp_kernel<8, 24><<<grid, kBlockThreads, 0, st>>>(ep);
   }
   return cudaGetLastError();
 }
@@ -1435,6 +1776,16 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   char* ws = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
 
+  // With the default schedule, a batch too small to give every resident narrow
+  // lane a few extensions would be bound by one lane's walk through its longest
+  // extension: route it to the warp-per-extension forms, whose antidiagonal
+  // latency is far lower.  An explicit schedule is followed as given.
+  if (sched == nullptr) {
+    const int wt = sch.narrow_band_cap;
+    const long long narrow_lanes =
+        (long long)D->sms * D->narrow_blocks[wt == 32 ? 0 : (wt == 48 ? 1 : 2)] * kBlockThreads;
+    if (2 * n_pairs < 4 * narrow_lanes) sch.narrow_max_xdrop = -1;
+  }
   record(st, 0);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
                         scoring, results, ws, L, sch, st);
@@ -1661,11 +2012,17 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       if (li == 0 && ci > 0) continue;  // all-wide ignores the narrow chunk
       rc = consider(c);
     }
-  // Stage 2: register slots of the warp form.
-  for (int ws = 16; ws <= 32 && rc == DIBELLA_OK; ws += 8) {
-    dibella_schedule_t c = cur;
-    c.wide_slots = ws;
-    rc = consider(c);
+  // Stage 2: lanes per extension (warp or 16/8-lane groups) x register slots of the wide form.
+  {
+    const dibella_schedule_t base2 = cur;
+    const int lanes[3] = {32, 16, 8};
+    for (int li = 0; li < 3 && rc == DIBELLA_OK; ++li)
+      for (int ws = 16; ws <= 32 && rc == DIBELLA_OK; ws += 8) {
+        dibella_schedule_t c = base2;
+        c.wide_group_lanes = lanes[li];
+        c.wide_slots = ws;
+        rc = consider(c);
+      }
   }
   // Stage 3: resident blocks per SM (occupancy maximum, or capped).
   for (int b = 1; b <= 3 && rc == DIBELLA_OK; ++b) {

@@ -34,12 +34,15 @@ def test_c1_all_pairs(c1, X):
 
 
 @pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "packed16", "packed24", "packed32",
-                                  "int16", "int32"])
+                                  "int16", "int32", "grp16x16", "grp16x24", "grp16x32", "grp8x16", "grp8x24"])
 @pytest.mark.parametrize("X", [0, 3, 7, 25])
 def test_every_kernel_form_matches(c1, form, X):
     """Route every extension to one form; escalations must reproduce the result."""
-    if form.startswith("packed"):
-        sched = schedule(wide_slots=int(form[6:]), wide_packed=1, **WIDE_ALL)
+    if form.startswith("grp"):
+        lanes, slots = form[3:].split("x")
+        sched = schedule(wide_group_lanes=int(lanes), wide_slots=int(slots), wide_packed=1, **WIDE_ALL)
+    elif form.startswith("packed"):
+        sched = schedule(wide_slots=int(form[6:]), wide_packed=1, wide_group_lanes=32, **WIDE_ALL)
     elif form.startswith("int"):
         sched = schedule(wide_slots=int(form[3:]), wide_packed=0, **WIDE_ALL)
     else:
@@ -105,7 +108,8 @@ def test_fuzz_medium(scoring):
         sc = scoring + (X,)
         exp = oracle_align(ascii, offs, pairs, k, sc)
         for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL),
-                      schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, **WIDE_ALL)):
+                      schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, wide_group_lanes=32, **WIDE_ALL),
+                      schedule(wide_group_lanes=16, **WIDE_ALL), schedule(wide_group_lanes=8, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
             assert_same(got, exp, "scoring %s X=%d" % (sc, X))
 
@@ -237,5 +241,7 @@ def test_packed_form_large_scores(c1, scoring, X):
     sc = scoring + (X,)
     exp = oracle_align(c1.reads, c1.offsets, pairs, 17, sc)
     for slots in (16, 24):
-        got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, sched=schedule(wide_slots=slots, **WIDE_ALL))
-        assert_same(got, exp, "scoring %s X=%d slots=%d" % (scoring, X, slots))
+        for lanes in (32, 16, 8):
+            got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc,
+                            sched=schedule(wide_slots=slots, wide_group_lanes=lanes, **WIDE_ALL))
+            assert_same(got, exp, "scoring %s X=%d slots=%d lanes=%d" % (scoring, X, slots, lanes))
