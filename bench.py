@@ -84,6 +84,19 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Barrier, then the maximum of `value` over all ranks (the step time of a
+    multi-GPU run is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -149,9 +162,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(w, seconds: float, xdrops):
     """The oracle, as it stands, on the host cores, over a bounded seeded sample
-    of the same workload, both X values; scaled to candidate pairs per second."""
+    of the same workload and X values; scaled to candidate pairs per second.
+    Also timed on one thread over a smaller sample."""
     import oracle
     threads = os.cpu_count() or 1
     probe = workloads.sample_pair_groups(w.pairs, 300, seed=17)
@@ -168,8 +194,16 @@ def cpu_baseline(w, seconds: float, xdrops):
         cells += int(r["cells"].sum())
     dt = time.perf_counter() - t0
     n_cand = len(workloads.pair_groups(sample)) - 1
+    # one thread, on a sample a quarter of the time budget long
+    n1 = max(20, int(n_groups * 0.25 / threads))
+    s1 = workloads.sample_pair_groups(w.pairs, n1, seed=19)
+    t1 = time.perf_counter()
+    for X in xdrops:
+        oracle.xdrop_batch(w.reads, w.offsets, s1, K, 1, -1, -1, X, n_threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": len(xdrops) * n_cand / dt, "unit": "aligned pairs/s", "cores": threads, "kind": "oracle",
-            "gcups": cells / dt / 1e9,
+            "gcups": cells / dt / 1e9, "cpu_model": cpu_model(),
+            "value_1_thread": len(xdrops) * (len(workloads.pair_groups(s1)) - 1) / dt1,
             "sample": "%d candidate pairs (%d seed records) drawn with seed 18 from the %s workload, "
                       "aligned at X=%s by the plain C++ oracle on %d host threads, %.1f s"
                       % (n_cand, len(sample), w.name, ",".join(map(str, xdrops)), threads, dt)}
@@ -258,8 +292,9 @@ def mode_tune(args):
     c_tuned = dib.dibella_batch_counters(al.workspace, stream=stream)
     cells = sum(c_tuned[c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global"))
     n_cand = len(workloads.pair_groups(pairs)) - 1
+    cpu = None if args.no_cpu else cpu_baseline(w, args.cpu_seconds, (X,))
     print(json.dumps({
-        "metric": "aligned pairs/s", "mode": "tune", "unit": "aligned pairs/s", "n_gpus": 1,
+        "metric": "aligned pairs/s", "mode": "tune", "cpu_baseline": cpu, "unit": "aligned pairs/s", "n_gpus": 1,
         "value": n_cand / (tuned_ms * 1e-3), "higher_is_better": True, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "c3_uneven", "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n,
                    "extensions": 2 * n, "xdrop": X, "scoring": "+1/-1/-1", "k": K, "steps": args.steps,
@@ -309,8 +344,9 @@ def mode_stream(args):
     cells = int(res["cells"].sum())
     n_cand = len(workloads.pair_groups(pairs)) - 1
     dt = float(np.median(runs))
+    cpu = None if args.no_cpu else cpu_baseline(w, args.cpu_seconds, (X,))
     print(json.dumps({
-        "metric": "aligned pairs/s", "mode": "stream", "value": n_cand / dt, "unit": "aligned pairs/s", "n_gpus": 1,
+        "metric": "aligned pairs/s", "mode": "stream", "cpu_baseline": cpu, "value": n_cand / dt, "unit": "aligned pairs/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "int32", "data": "synthetic", "gcups": cells / dt / 1e9,
         "config": {"workload": "c4_repeats_small (5 Mb genome = 1/20 of the configured 100 Mb)",
                    "reads": int(w.n_reads), "bases": int(len(w.reads)), "candidate_pairs": n_cand, "seed_records": n,
@@ -452,12 +488,7 @@ def main():
     with ClockSampler(local) as clocks:
         step_ms = [one_step(log) for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
-    my_ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([my_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        my_ms = float(t.item())
-        torch.distributed.barrier()
+    my_ms = max_over_ranks(float(np.mean(step_ms)), device=dev)
 
     # Verify the graph replays produced the same results as a direct call.
     res_graph = al.results_host(n_seeds).copy()
