@@ -364,6 +364,14 @@ __device__ __forceinline__ unsigned pk_pair(int lo, int hi) {
   return ((unsigned)lo & 0xFFFFu) | ((unsigned)hi << 16);
 }
 __device__ __forceinline__ int pk_lo(unsigned v) { return (int)(short)(v & 0xFFFFu); }
+// 0xFFFF in each 16-bit half of x whose top bit (bit 15 / bit 31) is set, else
+// 0: PTX prmt with sign-replicating selectors (byte 1's sign into bytes 0-1,
+// byte 3's sign into bytes 2-3).
+__device__ __forceinline__ unsigned half_sign_mask(unsigned x) {
+  unsigned r;
+  asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(r) : "r"(x));
+  return r;
+}
 __device__ __forceinline__ int pk_hi(unsigned v) { return (int)(short)(v >> 16); }
 
 template <int NC>
@@ -376,6 +384,11 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
   const int m = it.m, n = it.n;
   const long long a_lo = it.a0 - 1;
   const long long b_lo = it.b0 + 1;
+  // The lowest chunk's fresh b base is read every antidiagonal: address it with
+  // 32-bit offsets from a word pointer below every index it can take.
+  const long long b_floor = (b_lo - n - 128) & ~15ll;
+  const uint32_t* __restrict__ bwords = words + (b_floor >> 4);
+  const int b_rel = (int)(b_lo - b_floor);
   unsigned H[NC], Up[NC], Aw[NW], Bw[NW];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
@@ -452,7 +465,8 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     const int wtop = ntop >> 3;
     unsigned MM[NW];
     {
-      const int bfresh = base_of(words, b_lo - d + 64 * c0);  // lane 0, low cell of slot 1
+      const int r = b_rel - d + 64 * c0;  // lane 0, low cell of slot 1: store index b_lo - d + 64*c0
+      const int bfresh = (int)((__ldg(bwords + (r >> 4)) >> ((unsigned)(r & 15) * 2u)) & 3u);
       unsigned prev_top = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
@@ -493,19 +507,20 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     constexpr int s_ = DIBELLA_PK_I(S), p_ = s_ > 0 ? s_ - 1 : 0;                                  \
     const unsigned prevH = __shfl_sync(kFull, top_lane ? H[p_] : H[s_], src_lane);                 \
     const unsigned u2 = __byte_perm(H[s_], prevH, 0x1076u);                                        \
-    const unsigned bits = (MM[s_ >> 3] >> (2 * (s_ & 7))) & 0x00010001u;                           \
-    const unsigned sub2 = ((bits * 0xFFFFu) & S2) | (~(bits * 0xFFFFu) & M2);                      \
+    /* mismatch flags of the two cells moved to bits 15 and 31, then spread */                     \
+    const unsigned mis = half_sign_mask(MM[s_ >> 3] << (15 - 2 * (s_ & 7)));                       \
+    const unsigned sub2 = (mis & S2) | (~mis & M2);                                                \
     const unsigned ds = __viaddmax_s16x2(Up[s_], sub2, kNeg2);                                     \
     unsigned h2 = __viaddmax_s16x2(__vmaxs2(u2, H[s_]), G2, ds);                                   \
     const unsigned f = __vimin3_s16x2(__vadd2(h2, nthr2), __vadd2(A2, 0x00400040u * s_),          \
                                       __vsub2(B2, 0x00400040u * s_));                              \
-    const unsigned dead = ((f >> 15) & 0x00010001u) * 0xFFFFu;                                     \
+    const unsigned dead = half_sign_mask(f); /* 0xFFFF in every half with f < 0 */                 \
     h2 = (h2 & ~dead) | (kNeg2 & dead);                                                            \
     Up[s_] = u2;                                                                                   \
     H[s_] = h2;                                                                                    \
     vmax2 = __vmaxs2(vmax2, h2);                                                                   \
-    const unsigned blo_ = __ballot_sync(kFull, (h2 & 0xFFFFu) != 0xC000u);                         \
-    const unsigned bhi_ = __ballot_sync(kFull, (h2 >> 16) != 0xC000u);                             \
+    const unsigned blo_ = __ballot_sync(kFull, (dead & 1u) == 0);                                  \
+    const unsigned bhi_ = __ballot_sync(kFull, (dead >> 31) == 0);                                 \
     if (blo_ | bhi_) {                                                                             \
       any_slots |= 1u << s_;                                                                       \
       const int base_ = 64 * (cbase + s_);                                                         \
@@ -553,13 +568,14 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     cells += hi - lo + 1;
     if (any_slots == 0) break;
     const int vrel = __reduce_max_sync(kFull, max(pk_lo(vmax2), pk_hi(vmax2)));
-    const int sl = __ffs(any_slots) - 1, sh = 31 - __clz(any_slots);
     if (vrel + rb > best) {
+      const int sl = __ffs(any_slots) - 1, sh = 31 - __clz(any_slots);
       const unsigned v2 = pk_pair(vrel, vrel);
       int cand = INT32_MAX;
 #pragma unroll
       for (int s = 1; s < NC; ++s) {
-        if (s >= sl && s <= sh) {
+        if (s > sh) break;
+        if (s >= sl) {
           const unsigned e = H[s] ^ v2;
           const unsigned blo = __ballot_sync(kFull, (e & 0xFFFFu) == 0);
           const unsigned bhi = __ballot_sync(kFull, (e >> 16) == 0);

@@ -245,3 +245,22 @@ def test_packed_form_large_scores(c1, scoring, X):
             got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc,
                             sched=schedule(wide_slots=slots, wide_group_lanes=lanes, **WIDE_ALL))
             assert_same(got, exp, "scoring %s X=%d slots=%d lanes=%d" % (scoring, X, slots, lanes))
+
+
+@pytest.mark.parametrize("name,X,n_check", [("c3_uneven", 50, 120), ("c4_repeats_small", 15, 400)])
+def test_full_batch_sampled(name, X, n_check):
+    """The uneven-length (X = 50) and repeat-rich (X = 15) batches launched whole,
+    as the benchmark runs them; a seeded sample of records recomputed by the
+    oracle one by one."""
+    w = workloads.generate(name)
+    rng = np.random.default_rng(13)
+    idx = np.sort(rng.choice(len(w.pairs), n_check, replace=False))
+    sc = (1, -1, -1, X)
+    got = gpu_align(w.reads, w.offsets, w.pairs, 17, sc)
+    exp = oracle_align(w.reads, w.offsets, w.pairs[idx], 17, sc)
+    sub = got[idx].copy()
+    sub["status"] &= ~4
+    e2 = exp.copy()
+    e2["status"] &= ~4
+    assert_same(sub, e2, "%s sample X=%d" % (name, X))
+    assert ((got["status"] & 8) != 0).sum() == 0
