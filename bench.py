@@ -279,7 +279,8 @@ def mode_tune(args):
     with ClockSampler(0) as clocks:
         fixed_ms = _time_direct(torch, al, n, sc, stream, fixed, args.steps)
         c_fixed = dib.dibella_batch_counters(al.workspace, stream=stream)
-        sample = workloads.sample_pair_groups(pairs, max(1, (len(workloads.pair_groups(pairs)) - 1) // 10), seed=31)
+        sample = workloads.stratified_pair_groups(pairs, w.read_lengths,
+                                                  max(1, (len(workloads.pair_groups(pairs)) - 1) // 10))
         tal = dib.Aligner(store, len(sample), k=K, device=dev)
         tal.upload_pairs(sample)
         t0 = time.perf_counter()
@@ -304,7 +305,8 @@ def mode_tune(args):
         "tuned": {"schedule": best.as_dict(), "ms": tuned_ms, "pairs_per_s": n_cand / (tuned_ms * 1e-3),
                   "gcups": cells / (tuned_ms * 1e-3) / 1e9, "counters": c_tuned, "sample_ms": best_ms,
                   "schedules_tried": tried, "tuning_s": tune_s,
-                  "sample": "%d candidate pairs (10%%, seed 31)" % (len(workloads.pair_groups(sample)) - 1)},
+                  "sample": "%d candidate pairs (every 10th by decreasing min read length)"
+                            % (len(workloads.pair_groups(sample)) - 1)},
         "speedup_tuned_vs_fixed": fixed_ms / tuned_ms,
         "clocks": clocks.summary(),
     }))

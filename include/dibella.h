@@ -126,9 +126,11 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  *           packed as int16 pairs when wide_packed is set and
  *           xdrop <= 8000 (exact: scores are kept relative to a moving base),
  *           else 32 int32 cells of one warp;
- * an extension whose band outgrows its form is re-run from the start by a
- * warp with a 4096-cell shared-memory band, and beyond that by a warp whose
- * band lives in the workspace (sized by max_read_len: it cannot overflow).
+ * an extension whose band outgrows its form is re-run from the start by the
+ * next wider form: the narrow form's by the wide form, the wide form's by
+ * the next rung of 8 -> 16 -> 24 -> 32 slots, then by a warp with a
+ * 4096-cell shared-memory band, and beyond that by a warp whose band lives
+ * in the workspace (sized by max_read_len: it cannot overflow).
  * An extension is routed to narrow when xdrop <= narrow_max_xdrop and
  * min(remaining A, remaining B) <= narrow_max_len.  When a call passes no
  * schedule, batches with fewer than 4 extensions per resident narrow lane go
@@ -141,7 +143,8 @@ typedef struct {
   int32_t narrow_max_xdrop;
   int32_t narrow_max_len;
   int32_t narrow_band_cap;
-  int32_t wide_slots;             /* 16, 24, 32, or 0 = 16 if xdrop <= 30     */
+  int32_t wide_slots;             /* 8 (packed, one warp only), 16, 24, 32,   */
+                                  /* or 0 = 8 if xdrop <= 30 else 24          */
                                   /* else 24                                  */
   int32_t wide_packed;            /* 1: int16-pair cells when xdrop <= 8000   */
   int32_t wide_group_lanes;       /* packed wide form: lanes per extension,   */
@@ -208,8 +211,8 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
  * that may not hold allocations of its own.  This entry point runs the same
  * alignment as dibella_xdrop_batch (same arguments, results and semantics,
  * default schedule) without any workspace from the caller and without
- * allocating.  Its scratch is one fixed array inside the library, 8,782,080
- * bytes (about 8.4 MiB), which every GPU that loads the library keeps until
+ * allocating.  Its scratch is one fixed array inside the library, 9,306,624
+ * bytes (about 8.9 MiB), which every GPU that loads the library keeps until
  * the process exits.
  * Limits: at most DIBELLA_NOALLOC_MAX_PAIRS seed records per call (more
  * returns DIBELLA_ENOMEM, with the reason in dibella_last_error(), and does

@@ -68,10 +68,15 @@ struct ExtOut {
 };
 static_assert(sizeof(ExtOut) == 24, "ext out is 24 bytes");
 
+// Queues: routed narrow / wide; narrow escalations (to the wide form); one
+// queue per step of the wide-form slot ladder (8 -> 16 -> 24 -> 32 slots);
+// the shared-memory form's input; the global-band form's input.
+enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQLadder = 3, kQSmem = 7, kQGlobal = 8, kNumQ = 9 };
+
 struct Counters {
-  unsigned int tail[5];   // queue sizes (see the kQ* names)
-  unsigned int head[5];   // pop cursors
-  unsigned int pad_;
+  unsigned int tail[kNumQ];   // queue sizes (see the kQ* names)
+  unsigned int head[kNumQ];   // pop cursors
+  unsigned int pad_[2];
   unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
   unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / wide /
@@ -79,10 +84,7 @@ struct Counters {
   unsigned long long cells[4];  // cells of finished extensions: narrow, wide pass 1, wide pass 2, global
 };
 
-// Queues: routed narrow / wide; narrow escalations (to the wide form);
-// wide escalations (to the shared-memory form); shared-memory escalations
-// (to the global-band form).
-enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQEsc2 = 3, kQEsc3 = 4, kNumQ = 5 };
+
 
 struct Scoring {
   int M, S, G, X;
@@ -1387,7 +1389,7 @@ thread_local std::string g_last_error;
 
 std::mutex g_mu;
 dibella_schedule_t g_default_schedule = {
-    /*narrow_max_xdrop=*/16, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/64,
+    /*narrow_max_xdrop=*/10, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
     /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
@@ -1397,7 +1399,7 @@ struct DeviceInfo {
   int sms = 0;
   int narrow_blocks[3] = {0, 0, 0};  // narrow_kernel<32/48/64> blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
-  int pk_blocks[3] = {0, 0, 0};      // wide_pk_kernel<16/24/32> blocks per SM
+  int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
   int grp16_blocks[3] = {0, 0, 0};   // wide_grp_kernel<16, 16/24/32> blocks per SM
   int grp8_blocks[2] = {0, 0};       // wide_grp_kernel<8, 16/24> blocks per SM
   int smem_blocks = 0;               // wide_smem_kernel blocks per SM
@@ -1489,6 +1491,7 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.pk_blocks[0], (const void*)wide_pk_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[1], (const void*)wide_pk_kernel<24>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[2], (const void*)wide_pk_kernel<32>, kBlockThreads, 0)) ||
+        (rc = occupancy(&D.pk_blocks[3], (const void*)wide_pk_kernel<8>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.grp16_blocks[0], (const void*)wide_grp_kernel<16, 16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.grp16_blocks[1], (const void*)wide_grp_kernel<16, 24>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.grp16_blocks[2], (const void*)wide_grp_kernel<16, 32>, kBlockThreads, 0)) ||
@@ -1504,7 +1507,9 @@ int device_info(DeviceInfo** out) {
 
 int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
-  if (s.wide_slots != 0 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32) return DIBELLA_EINVAL;
+  if (s.wide_slots != 0 && s.wide_slots != 8 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32)
+    return DIBELLA_EINVAL;
+  if (s.wide_slots == 8 && s.wide_group_lanes != 0 && s.wide_group_lanes != 32) return DIBELLA_EINVAL;
   if (s.wide_packed != 0 && s.wide_packed != 1) return DIBELLA_EINVAL;
   if (s.wide_group_lanes != 0 && s.wide_group_lanes != 8 && s.wide_group_lanes != 16 && s.wide_group_lanes != 32)
     return DIBELLA_EINVAL;
@@ -1564,9 +1569,10 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
   int lanes = sch.wide_group_lanes;
   if (lanes == 0) lanes = 32;  // auto: one warp per extension (measured fastest at X = 7..50)
   if (!packed) lanes = 32;                                      // the int32 form is one warp per extension
-  if (sch.wide_slots == 0) sch.wide_slots = (lanes == 32) ? (xdrop <= 30 ? 16 : 24) : (xdrop <= 30 ? 16 : 24);
+  if (sch.wide_slots == 0) sch.wide_slots = (lanes == 32 && packed) ? (xdrop <= 30 ? 8 : 24) : (xdrop <= 30 ? 16 : 24);
   if (lanes == 8 && sch.wide_slots == 32) sch.wide_slots = 24;
-  const int vi = sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2);
+  if (sch.wide_slots == 8 && (lanes != 32 || !packed)) sch.wide_slots = 16;
+  const int vi = sch.wide_slots == 8 ? 3 : (sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2));
   int b;
   if (!packed)
     b = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
@@ -1584,7 +1590,9 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
     else
       wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
   } else if (lanes == 32) {
-    if (vi == 0)
+    if (vi == 3)
+      wide_pk_kernel<8><<<grid, kBlockThreads, 0, st>>>(ep);
+    else if (vi == 0)
       wide_pk_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
     else if (vi == 1)
       wide_pk_kernel<24><<<grid, kBlockThreads, 0, st>>>(ep);
@@ -1607,13 +1615,28 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
 }
 
 // All extension launches of one batch, in stream order:
-//   narrow form   on Narrow (outgrown -> Esc1)
-//   wide form     on Wide   (outgrown -> Esc2)
-//   wide form     on Esc1   (outgrown -> Esc2)
-//   shared-memory form on Esc2 (outgrown -> Esc3)
-//   global form   on Esc3
-int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, int xdrop, ExtendParams ep,
+//   narrow form        on Narrow        (outgrown -> Esc1)
+//   wide form (S slots) on Wide, Esc1   (outgrown -> ladder queue of S)
+//   wide form, next rung of the slot ladder 8 -> 16 -> 24 -> 32, on the queue
+//                      of the rung below (outgrown -> its own queue)
+//   shared-memory form on Smem          (outgrown -> Global)
+//   global form        on Global
+// Every launch whose queue is empty returns at once.
+int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, ExtendParams ep,
                       int* const q[kNumQ], cudaStream_t st) {
+  dibella_schedule_t sch = sch_in;
+  const bool packed = sch.wide_packed && xdrop <= kPackedMaxX;
+  if (sch.wide_group_lanes == 0 || !packed) sch.wide_group_lanes = 32;
+  if (sch.wide_slots == 0) sch.wide_slots = (sch.wide_group_lanes == 32 && packed) ? (xdrop <= 30 ? 8 : 24)
+                                                                                 : (xdrop <= 30 ? 16 : 24);
+  if (sch.wide_slots == 8 && (sch.wide_group_lanes != 32 || !packed)) sch.wide_slots = 16;
+  if (sch.wide_group_lanes == 8 && sch.wide_slots == 32) sch.wide_slots = 24;
+  // ladder rungs above the configured slot count (the int32 form has 16 and 32 only)
+  int rungs[4], n_rungs = 0;
+  const int ladder[4] = {8, 16, 24, 32};
+  for (int r = 0; r < 4; ++r)
+    if (ladder[r] > sch.wide_slots && (packed || ladder[r] == 32)) rungs[n_rungs++] = ladder[r];
+  auto rung_queue = [&](int slots) { return kQLadder + (slots / 8 - 1); };  // 8..32 -> 3..6
   const int wt = sch.narrow_band_cap;
   const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
   int nb = D.narrow_blocks[vi];
@@ -1628,9 +1651,11 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, int xd
   if ((e = launch_narrow(wt, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
   record(st, 2);
 
+  // The configured wide form; its escalations climb the ladder.
   ep.narrow_q = nullptr;
-  ep.esc_q = q[kQEsc2];
-  ep.esc_q_id = kQEsc2;
+  int cur_q = n_rungs ? rung_queue(sch.wide_slots) : kQSmem;
+  ep.esc_q = q[cur_q];
+  ep.esc_q_id = cur_q;
   ep.wide_q = q[kQWide];
   ep.wide_q_id = kQWide;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
@@ -1638,16 +1663,28 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch, int xd
   ep.wide_q = q[kQEsc1];
   ep.wide_q_id = kQEsc1;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
+  for (int r = 0; r < n_rungs; ++r) {
+    dibella_schedule_t up = sch;
+    up.wide_slots = rungs[r];
+    up.wide_group_lanes = 32;
+    const int next_q = r + 1 < n_rungs ? rung_queue(rungs[r]) : kQSmem;
+    ep.wide_q = q[cur_q];
+    ep.wide_q_id = cur_q;
+    ep.esc_q = q[next_q];
+    ep.esc_q_id = next_q;
+    if ((e = launch_wide(D, up, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (ladder)");
+    cur_q = next_q;
+  }
 
-  ep.wide_q = q[kQEsc2];
-  ep.wide_q_id = kQEsc2;
-  ep.esc_q = q[kQEsc3];
-  ep.esc_q_id = kQEsc3;
+  ep.wide_q = q[kQSmem];
+  ep.wide_q_id = kQSmem;
+  ep.esc_q = q[kQGlobal];
+  ep.esc_q_id = kQGlobal;
   wide_smem_kernel<<<D.sms * D.smem_blocks, kSmemWarps * 32, kWideSmemBytes, st>>>(ep);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_smem launch");
 
-  ep.wide_q = q[kQEsc3];
-  ep.wide_q_id = kQEsc3;
+  ep.wide_q = q[kQGlobal];
+  ep.wide_q_id = kQGlobal;
   global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
   record(st, 4);
@@ -1716,6 +1753,7 @@ constexpr size_t kNoAllocBytes =
     up256(sizeof(Counters)) + up256(sizeof(Item) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(ExtOut) * 2 * kNoAllocMaxPairs) + kNumQ * up256(sizeof(int) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(int) * 3 * (size_t)kNoAllocBandCap * kGlobalWarps);
+static_assert(kNoAllocBytes == 9306624, "the size stated in include/dibella.h must follow the layout");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -2033,7 +2071,7 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
     const dibella_schedule_t base2 = cur;
     const int lanes[3] = {32, 16, 8};
     for (int li = 0; li < 3 && rc == DIBELLA_OK; ++li)
-      for (int ws = 16; ws <= 32 && rc == DIBELLA_OK; ws += 8) {
+      for (int ws = 8; ws <= 32 && rc == DIBELLA_OK; ws += 8) {
         dibella_schedule_t c = base2;
         c.wide_group_lanes = lanes[li];
         c.wide_slots = ws;

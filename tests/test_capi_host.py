@@ -94,7 +94,7 @@ def test_size_queries_validate():
 def test_schedule_validation():
     s = dib.dibella_get_default_schedule()
     d = s.as_dict()
-    assert d["narrow_band_cap"] in (32, 48, 64) and d["wide_slots"] in (0, 16, 24, 32)
+    assert d["narrow_band_cap"] in (32, 48, 64) and d["wide_slots"] in (0, 8, 16, 24, 32)
     bad = dib.Schedule.from_dict(dict(d, narrow_band_cap=40))
     with pytest.raises(dib.DibellaError):
         dib.dibella_set_default_schedule(bad)

@@ -33,7 +33,7 @@ def test_c1_all_pairs(c1, X):
     assert ((got["status"] & 4) != 0).sum() == len(workloads.pair_groups(c1.pairs)) - 1
 
 
-@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "packed16", "packed24", "packed32",
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "packed8", "packed16", "packed24", "packed32",
                                   "int16", "int32", "grp16x16", "grp16x24", "grp16x32", "grp8x16", "grp8x24"])
 @pytest.mark.parametrize("X", [0, 3, 7, 25])
 def test_every_kernel_form_matches(c1, form, X):

@@ -89,3 +89,14 @@ def test_serving_requests_shape():
     assert all(b > a for a, b in zip(times, times[1:]))
     for _, x, idx in reqs:
         assert x in (7, 25, 50) and len(idx) >= 1
+
+
+def test_stratified_sample_keeps_whole_pairs_and_longest():
+    w = workloads.generate("c1_tiny")
+    s = workloads.stratified_pair_groups(w.pairs, w.read_lengths, 50)
+    g = workloads.pair_groups(s)
+    assert len(g) - 1 == 50
+    L = w.read_lengths
+    key_all = np.minimum(L[w.pairs["read_a"]], L[w.pairs["read_b"]])
+    key_s = np.minimum(L[s["read_a"]], L[s["read_b"]])
+    assert key_s.max() == key_all.max()

@@ -214,6 +214,22 @@ def sample_pair_groups(pairs: np.ndarray, n_groups: int, seed: int) -> np.ndarra
     return pairs[idx]
 
 
+def stratified_pair_groups(pairs: np.ndarray, read_lengths: np.ndarray, n_groups: int) -> np.ndarray:
+    """Every k-th whole candidate pair in order of decreasing min(len_a, len_b):
+    a sample whose length mix (including the longest pairs) follows the batch."""
+    g = pair_groups(pairs)
+    n = len(g) - 1
+    if n == 0 or n_groups <= 0:
+        return pairs[:0]
+    starts = g[:-1]
+    key = np.minimum(read_lengths[pairs["read_a"][starts]], read_lengths[pairs["read_b"][starts]])
+    order = np.argsort(-key, kind="stable")
+    step = max(1, n // min(n_groups, n))
+    pick = np.sort(order[::step][:n_groups])
+    idx = np.concatenate([np.arange(g[i], g[i + 1]) for i in pick])
+    return pairs[idx]
+
+
 def serving_requests(pairs: np.ndarray, n_requests: int, rate_per_s: float, seed: int,
                      max_size: int = 4096, xdrops=(7, 25, 50)):
     """Poisson arrivals of requests, each a log-uniform number (1..max_size) of whole
