@@ -501,8 +501,12 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     // Band test as int16 pairs: a = i - lo >= 0 and b = hi - i >= 0.
     const int rel_lo = 2 * lane - (lo - 64 * cbase), rel_hi = (hi - 64 * cbase) - 2 * lane;
     const unsigned A2 = pk_pair(rel_lo, rel_lo + 1), B2 = pk_pair(rel_hi, rel_hi - 1);
-    unsigned vmax2 = kNeg2, any_slots = 0;
-    int first = INT32_MAX, last = -1;
+    // Live bits of this lane: word s/16, bit s%16 = low cell of slot s live,
+    // bit 16 + s%16 = high cell live (one LOP3 per slot, no vote).
+    constexpr int NL = (NC + 15) / 16;
+    unsigned vmax2 = kNeg2, lm[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) lm[q] = 0;
 #define DIBELLA_PK_I(S) ((S) < NC ? (S) : NC - 1)
 #define DIBELLA_PK_SLOT(S)                                                                         \
   if (S < NC) {                                                                                    \
@@ -521,14 +525,7 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     Up[s_] = u2;                                                                                   \
     H[s_] = h2;                                                                                    \
     vmax2 = __vmaxs2(vmax2, h2);                                                                   \
-    const unsigned blo_ = __ballot_sync(kFull, (dead & 1u) == 0);                                  \
-    const unsigned bhi_ = __ballot_sync(kFull, (dead >> 31) == 0);                                 \
-    if (blo_ | bhi_) {                                                                             \
-      any_slots |= 1u << s_;                                                                       \
-      const int base_ = 64 * (cbase + s_);                                                         \
-      first = base_ + min(blo_ ? 2 * __ffs(blo_) - 2 : 64, bhi_ ? 2 * __ffs(bhi_) - 1 : 64);      \
-      if (last < 0) last = base_ + max(blo_ ? 62 - 2 * __clz(blo_) : -1, bhi_ ? 63 - 2 * __clz(bhi_) : -1); \
-    }                                                                                              \
+    lm[s_ >> 4] |= ~dead & (0x00010001u << (s_ & 15));                                             \
   }
     switch (ntop) {
       case 31: DIBELLA_PK_SLOT(31) [[fallthrough]];
@@ -568,10 +565,32 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
 #undef DIBELLA_PK_I
     H[0] = kNeg2;
     cells += hi - lo + 1;
-    if (any_slots == 0) break;
+    // Lowest and highest live cell of the lane (relative to chunk cbase), then of
+    // the warp: two reductions per antidiagonal.
+    int my_first = INT32_MAX, my_last = -1;
+#pragma unroll
+    for (int q = NL - 1; q >= 0; --q) {
+      const unsigned comb = (lm[q] | (lm[q] >> 16)) & 0xFFFFu;
+      if (comb) {
+        const int s_lo = __ffs(comb) - 1;
+        my_first = 64 * (16 * q + s_lo) + 2 * lane + (int)(((lm[q] >> s_lo) & 1u) ^ 1u);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const unsigned comb = (lm[q] | (lm[q] >> 16)) & 0xFFFFu;
+      if (comb) {
+        const int s_hi = 31 - __clz(comb);
+        my_last = 64 * (16 * q + s_hi) + 2 * lane + (int)((lm[q] >> (16 + s_hi)) & 1u);
+      }
+    }
+    const int last_rel = __reduce_max_sync(kFull, my_last);
+    if (last_rel < 0) break;
+    const int first_rel = __reduce_min_sync(kFull, my_first);
+    const int first = 64 * cbase + first_rel, last = 64 * cbase + last_rel;
     const int vrel = __reduce_max_sync(kFull, max(pk_lo(vmax2), pk_hi(vmax2)));
     if (vrel + rb > best) {
-      const int sl = __ffs(any_slots) - 1, sh = 31 - __clz(any_slots);
+      const int sl = first_rel >> 6, sh = last_rel >> 6;
       const unsigned v2 = pk_pair(vrel, vrel);
       int cand = INT32_MAX;
 #pragma unroll
