@@ -1408,7 +1408,7 @@ thread_local std::string g_last_error;
 
 std::mutex g_mu;
 dibella_schedule_t g_default_schedule = {
-    /*narrow_max_xdrop=*/10, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
+    /*narrow_max_xdrop=*/30, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
     /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
@@ -1852,12 +1852,17 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   // With the default schedule, a batch too small to give every resident narrow
   // lane a few extensions would be bound by one lane's walk through its longest
   // extension: route it to the warp-per-extension forms, whose antidiagonal
-  // latency is far lower.  An explicit schedule is followed as given.
+  // latency is far lower.  Above X = 10 the narrow lanes also hand every
+  // extension whose band passes the cap to the wide form, which can start only
+  // after the narrow launch ends; unless the batch gives each lane 16 or more
+  // extensions, the long ones (key above 5000) go straight to the wide form.
+  // An explicit schedule is followed as given.
   if (sched == nullptr) {
     const int wt = sch.narrow_band_cap;
     const long long narrow_lanes =
         (long long)D->sms * D->narrow_blocks[wt == 32 ? 0 : (wt == 48 ? 1 : 2)] * kBlockThreads;
     if (2 * n_pairs < 4 * narrow_lanes) sch.narrow_max_xdrop = -1;
+    else if (scoring.xdrop > 10 && 2 * n_pairs < 16 * narrow_lanes) sch.narrow_max_len = min(sch.narrow_max_len, 5000);
   }
   record(st, 0);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
