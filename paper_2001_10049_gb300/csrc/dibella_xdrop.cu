@@ -365,6 +365,8 @@ constexpr int kRebase = 4096;
 __device__ __forceinline__ unsigned pk_pair(int lo, int hi) {
   return ((unsigned)lo & 0xFFFFu) | ((unsigned)hi << 16);
 }
+// x in both 16-bit halves (x within int16)
+__device__ __forceinline__ unsigned pk_dup(int x) { return __byte_perm((unsigned)x, 0u, 0x1010u); }
 __device__ __forceinline__ int pk_lo(unsigned v) { return (int)(short)(v & 0xFFFFu); }
 // 0xFFFF in each 16-bit half of x whose top bit (bit 15 / bit 31) is set, else
 // 0: PTX prmt with sign-replicating selectors (byte 1's sign into bytes 0-1,
@@ -414,53 +416,69 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     Bw[0] = (b0b << 2) | (b1b << 18);
   }
   int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  int bq_idx = INT32_MIN;  // store word of the fresh b base, cached
+  unsigned bq = 0;
   long long cells = 0;
   for (int d = 1; d <= m + n; ++d) {
     const int lo = max(live_lo, d - n);
     const int hi = min(min(live_hi + 1, d), m);
     const int c0 = lo >> 6;
-    while (cbase < c0 - 1) {  // keep slot 0 = chunk c0 - 1
-#pragma unroll
-      for (int s = 0; s + 1 < NC; ++s) {
-        H[s] = H[s + 1];
-        Up[s] = Up[s + 1];
-      }
-      H[NC - 1] = kNeg2;
-      Up[NC - 1] = kNeg2;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const int wn = w + 1 < NW ? w + 1 : w;
-        const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
-        Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
-        Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
-      }
-      ++cbase;
-    }
     const int cneed = (hi + 1) >> 6;
-    if (cneed - cbase > NC - 1) return false;
-    if (cneed > ctop) {  // activate the chunk holding hi + 1 (at most one per antidiagonal)
-      const int snew = cneed - cbase;
-      const int i0 = 64 * cneed + 2 * lane;
-      const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
-      const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
-      const int sh = 2 * (snew & 7);
-      const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
+    // Window moves, chunk (de)activation and rebasing are rare: one test for all.
+    if ((c0 - 1 != cbase) | (cneed != ctop) | (best - rb >= kRebase)) {
+      while (cbase < c0 - 1) {  // keep slot 0 = chunk c0 - 1
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        if (w == (snew >> 3)) {
-          Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
-          Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+        for (int s = 0; s + 1 < NC; ++s) {
+          H[s] = H[s + 1];
+          Up[s] = Up[s + 1];
+        }
+        H[NC - 1] = kNeg2;
+        Up[NC - 1] = kNeg2;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int wn = w + 1 < NW ? w + 1 : w;
+          const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
+          Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
+          Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
+        }
+        ++cbase;
+      }
+      if (cneed - cbase > NC - 1) return false;
+      if (cneed > ctop) {  // activate the chunk holding hi + 1 (at most one per antidiagonal)
+        const int snew = cneed - cbase;
+        const int i0 = 64 * cneed + 2 * lane;
+        const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
+        const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
+        const int sh = 2 * (snew & 7);
+        const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          if (w == (snew >> 3)) {
+            Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
+            Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+          }
+        }
+#pragma unroll
+        for (int s = 1; s < NC; ++s) {
+          if (s == snew) {
+            H[s] = kNeg2;
+            Up[s] = kNeg2;
+          }
         }
       }
+      ctop = cneed;
+      // Rebase the packed scores when the best has run 4096 above the base.
+      if (best - rb >= kRebase) {
+        const int delta = best - rb;
+        const unsigned dn = pk_pair(-delta, -delta);
 #pragma unroll
-      for (int s = 1; s < NC; ++s) {
-        if (s == snew) {
-          H[s] = kNeg2;
-          Up[s] = kNeg2;
+        for (int s = 0; s < NC; ++s) {
+          H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
+          Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
         }
+        rb = best;
       }
     }
-    ctop = cneed;
     // Move every b base to the next cell (cell i takes the base of cell i-1),
     // for the words that hold active slots, and form their mismatch bits.
     const int ntop = ctop - cbase;
@@ -468,7 +486,11 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     unsigned MM[NW];
     {
       const int r = b_rel - d + 64 * c0;  // lane 0, low cell of slot 1: store index b_lo - d + 64*c0
-      const int bfresh = (int)((__ldg(bwords + (r >> 4)) >> ((unsigned)(r & 15) * 2u)) & 3u);
+      if ((r >> 4) != bq_idx) {  // r falls by one per antidiagonal: one load per 16
+        bq_idx = r >> 4;
+        bq = __ldg(bwords + bq_idx);
+      }
+      const int bfresh = (int)((bq >> ((unsigned)(r & 15) * 2u)) & 3u);
       unsigned prev_top = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
@@ -485,22 +507,12 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
         }
       }
     }
-    // Rebase the packed scores when the best has run 4096 above the base.
-    if (best - rb >= kRebase) {
-      const int delta = best - rb;
-      const unsigned dn = pk_pair(-delta, -delta);
-#pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
-        Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
-      }
-      rb = best;
-    }
     const int thr_rel = best - rb - sc.X;
     const unsigned nthr2 = pk_pair(-thr_rel, -thr_rel);
     // Band test as int16 pairs: a = i - lo >= 0 and b = hi - i >= 0.
-    const int rel_lo = 2 * lane - (lo - 64 * cbase), rel_hi = (hi - 64 * cbase) - 2 * lane;
-    const unsigned A2 = pk_pair(rel_lo, rel_lo + 1), B2 = pk_pair(rel_hi, rel_hi - 1);
+    const unsigned lane2 = pk_pair(2 * lane, 2 * lane + 1);  // the lane's two cell offsets
+    const unsigned A2 = __vsub2(lane2, pk_dup(lo - 64 * cbase));
+    const unsigned B2 = __vsub2(pk_dup(hi - 64 * cbase), lane2);
     // Live bits of this lane: word s/16, bit s%16 = low cell of slot s live,
     // bit 16 + s%16 = high cell live (one LOP3 per slot, no vote).
     constexpr int NL = (NC + 15) / 16;
