@@ -135,10 +135,10 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  * min(remaining A, remaining B) <= narrow_max_len.  When a call passes no
  * schedule, batches with fewer than 4 extensions per resident narrow lane go
  * entirely to the wide form (they would wait on one lane's longest
- * extension), and for xdrop > 10 batches with fewer than 16 per lane send
- * keys above 5000 to the wide form (a narrow lane would otherwise hold up
- * the escalations behind its long extension); an explicit schedule is
- * followed as given.  Work is ordered by
+ * extension), and for xdrop > 10 keys above 20000 (above 5000 in batches
+ * with fewer than 16 extensions per lane) go to the wide form (a narrow lane
+ * would otherwise hold up the escalations behind its long extension); an
+ * explicit schedule is followed as given.  Work is ordered by
  * n_buckets length buckets (longest first); bucket b holds keys below
  * bucket_bounds[b] (ascending), the last bucket everything else. */
 #define DIBELLA_MAX_BUCKETS 8

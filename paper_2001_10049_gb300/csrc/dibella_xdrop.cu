@@ -638,25 +638,46 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
 // ---------------------------------------------------------------------------
 // Narrow form: one lane per extension.  Two antidiagonal arrays of WT cells
 // per lane, lane-interleaved in shared memory (cell slot s of array A of a
-// lane at word ((A*WT + s) * 32 + lane), so the 32 lanes never conflict).
+// lane at element ((A*WT + s) * 32 + lane), so the 32 lanes never conflict).
 // Slot s holds cell i = f + s; the frame f moves up when the band reaches the
 // top.  The band is walked cell by cell; the array of d-2 is overwritten in
 // place with d (its value is read one cell ahead).
+// Cells are stored as T: int32 scores, or (for X <= kNarrow16MaxX) int16
+// scores relative to a per-lane base rb, rebased when the best has run 4096
+// above it.  As in the packed wide form this is exact: live values then lie in
+// [-X, 4096 + 64] of rb and dead cells hold -16384, so the halved rows (and the
+// doubled residency they allow) change no result.
+template <typename T>
+struct NarrowCell;
+template <>
+struct NarrowCell<int> {
+  static constexpr int kDead = kNeg;
+  static constexpr bool kRelative = false;
+};
+template <>
+struct NarrowCell<short> {
+  static constexpr int kDead = -16384;
+  static constexpr bool kRelative = true;
+};
+constexpr int kNarrow16MaxX = 8000;
+constexpr int kNarrowRebase = 4096;
+
 template <int WT>
 struct NarrowLane {
   long long a0, b0;
   int m, n, item;
-  int d, live_lo, live_hi, best, bi, bj, f, h1;
+  int d, live_lo, live_hi, best, bi, bj, f, h1, rb;
   long long cells;
 };
 
-template <int WT>
-__device__ __forceinline__ int& nslot(int* wbase, int A, int s, int lane) {
+template <int WT, typename T>
+__device__ __forceinline__ T& nslot(T* wbase, int A, int s, int lane) {
   return wbase[((A * WT + s) << 5) + lane];
 }
 
-template <int WT>
-__device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, int* wbase, int lane) {
+template <int WT, typename T>
+__device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, T* wbase, int lane) {
+  constexpr int kD = NarrowCell<T>::kDead;
   L.a0 = it.a0;
   L.b0 = it.b0;
   L.m = it.m;
@@ -670,19 +691,21 @@ __device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, int* wb
   L.bj = 0;
   L.f = -1;
   L.h1 = 0;
+  L.rb = 0;
   L.cells = 0;
-  nslot<WT>(wbase, 0, 0, lane) = kNeg;  // d = 0: i = -1
-  nslot<WT>(wbase, 0, 1, lane) = 0;     //        i = 0
-  nslot<WT>(wbase, 0, 2, lane) = kNeg;  //        i = 1
-  nslot<WT>(wbase, 1, 0, lane) = kNeg;  // d = -1: i = -1
-  nslot<WT>(wbase, 1, 1, lane) = kNeg;  //         i = 0
+  nslot<WT>(wbase, 0, 0, lane) = (T)kD;  // d = 0: i = -1
+  nslot<WT>(wbase, 0, 1, lane) = (T)0;   //        i = 0
+  nslot<WT>(wbase, 0, 2, lane) = (T)kD;  //        i = 1
+  nslot<WT>(wbase, 1, 0, lane) = (T)kD;  // d = -1: i = -1
+  nslot<WT>(wbase, 1, 1, lane) = (T)kD;  //         i = 0
 }
 
 // One antidiagonal for one lane.  Returns 1 when the extension finished,
 // 2 when its band outgrew the lane's storage, 0 otherwise.
-template <int WT>
+template <int WT, typename T>
 __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words, const Scoring sc,
-                           int* wbase, int lane) {
+                           T* wbase, int lane) {
+  constexpr int kD = NarrowCell<T>::kDead;
   const int d = L.d;
   const int lo = max(L.live_lo, d - L.n);
   const int hi = min(min(L.live_hi + 1, d), L.m);
@@ -694,11 +717,21 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
     for (int i = lo - 1; i <= hi - 1; ++i) nslot<WT>(wbase, h2, i - nf, lane) = nslot<WT>(wbase, h2, i - L.f, lane);
     L.f = nf;
   }
+  if (NarrowCell<T>::kRelative && L.best - L.rb >= kNarrowRebase) {
+    // Both rows, every slot: live values stay above -X, dead ones stay dead.
+    const int delta = L.best - L.rb;
+    for (int A = 0; A < 2; ++A)
+      for (int t = 0; t < WT; ++t) {
+        T& c = nslot<WT>(wbase, A, t, lane);
+        c = (T)max((int)c - delta, kD);
+      }
+    L.rb = L.best;
+  }
   const int f = L.f;
-  const int thr = L.best - sc.X;
+  const int thr = L.best - L.rb - sc.X;
   int u = nslot<WT>(wbase, h1, lo - 1 - f, lane);
   int dg = nslot<WT>(wbase, h2, lo - 1 - f, lane);
-  int vmax = kNeg;
+  int vmax = kD;
   const long long abase = L.a0 - 1, bbase = L.b0 + 1 - d;
   for (int i = lo; i <= hi; i += 16) {
     const uint32_t wa = base_window(words, abase + i);
@@ -706,8 +739,8 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
     const uint32_t x = ~(wa ^ wb);
     const uint32_t mm = (x | (x >> 1)) & 0x55555555u;
     const int cnt = min(16, hi - i + 1);
-    int* p1 = &nslot<WT>(wbase, h1, i - f, lane);
-    int* p2 = &nslot<WT>(wbase, h2, i - f, lane);
+    T* p1 = &nslot<WT>(wbase, h1, i - f, lane);
+    T* p2 = &nslot<WT>(wbase, h2, i - f, lane);
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
       if (t < cnt) {
@@ -715,27 +748,27 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
         const int dn = p2[t * 32];
         const int sub = ((mm >> (2 * t)) & 1u) ? sc.S : sc.M;
         int h = max(max(u, lf) + sc.G, dg + sub);
-        h = h >= thr ? h : kNeg;
-        p2[t * 32] = h;
+        h = h >= thr ? h : kD;
+        p2[t * 32] = (T)h;
         vmax = max(vmax, h);
         u = lf;
         dg = dn;
       }
     }
   }
-  nslot<WT>(wbase, h2, lo - 1 - f, lane) = kNeg;
-  nslot<WT>(wbase, h2, hi + 1 - f, lane) = kNeg;
+  nslot<WT>(wbase, h2, lo - 1 - f, lane) = (T)kD;
+  nslot<WT>(wbase, h2, hi + 1 - f, lane) = (T)kD;
   L.cells += hi - lo + 1;
   L.h1 = h2;
-  if (vmax == kNeg) return 1;
+  if (vmax == kD) return 1;
   int llo = lo;
-  while (nslot<WT>(wbase, h2, llo - f, lane) == kNeg) ++llo;
+  while ((int)nslot<WT>(wbase, h2, llo - f, lane) == kD) ++llo;
   int lhi = hi;
-  while (nslot<WT>(wbase, h2, lhi - f, lane) == kNeg) --lhi;
-  if (vmax > L.best) {
+  while ((int)nslot<WT>(wbase, h2, lhi - f, lane) == kD) --lhi;
+  if (vmax + L.rb > L.best) {
     int b = llo;
-    while (nslot<WT>(wbase, h2, b - f, lane) != vmax) ++b;
-    L.best = vmax;
+    while ((int)nslot<WT>(wbase, h2, b - f, lane) != vmax) ++b;
+    L.best = vmax + L.rb;
     L.bi = b;
     L.bj = d - b;
   }
@@ -774,8 +807,11 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
 }
 
 // Packed form, one warp per extension (routed here only when X <= kPackedMaxX).
+// The 8-slot form asks for 9 resident CTAs per SM: measured a little faster than
+// the unconstrained allocation (8 CTAs) and than 10 or 12 (the slot code then
+// recomputes values it can no longer keep in registers).
 template <int NC>
-__global__ void __launch_bounds__(kBlockThreads) wide_pk_kernel(ExtendParams p) {
+__global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : 1) wide_pk_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   for (;;) {
@@ -1133,12 +1169,12 @@ __global__ void __launch_bounds__(kSmemWarps * 32) wide_smem_kernel(ExtendParams
 }
 
 // Narrow form: one lane per extension; lanes refill independently.  Each warp
-// owns 2*WT*32 ints of shared memory (see NarrowLane).
-template <int WT>
+// owns 2*WT*32 cells of type T in shared memory (see NarrowLane).
+template <int WT, typename T>
 __global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
-  extern __shared__ int smem[];
+  extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
-  int* wbase = smem + (threadIdx.x >> 5) * (2 * WT * 32);
+  T* wbase = reinterpret_cast<T*>(smem_words) + (threadIdx.x >> 5) * (2 * WT * 32);
   const unsigned ntail = *((volatile unsigned*)&p.cnt->tail[p.narrow_q_id]);
   NarrowLane<WT> L;
   bool active = false, exhausted = false;
@@ -1154,7 +1190,7 @@ __global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
         if (q < ntail) {
           const int item = p.narrow_q[q];
           const Item it = p.items[item];
-          narrow_init<WT>(L, it, item, wbase, lane);
+          narrow_init<WT, T>(L, it, item, wbase, lane);
           active = true;
           if (it.m + it.n == 0) {
             ExtOut o;
@@ -1172,7 +1208,7 @@ __global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
       continue;
     }
     if (active) {
-      const int r = narrow_step<WT>(L, p.words, p.sc, wbase, lane);
+      const int r = narrow_step<WT, T>(L, p.words, p.sc, wbase, lane);
       if (r == 1) {
         ExtOut o;
         o.best = L.best; o.i_end = L.bi; o.j_end = L.bj; o.status = 0; o.cells = L.cells;
@@ -1428,7 +1464,7 @@ dibella_schedule_t g_default_schedule = {
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
-  int narrow_blocks[3] = {0, 0, 0};  // narrow_kernel<32/48/64> blocks per SM
+  int narrow_blocks[2][3] = {};  // narrow_kernel<32/48/64, int | short> blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
   int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
   int grp16_blocks[3] = {0, 0, 0};   // wide_grp_kernel<16, 16/24/32> blocks per SM
@@ -1486,9 +1522,9 @@ int gcap_from_workspace(long long n_pairs, long long bytes) {
   return best;
 }
 
-template <int WT>
+template <int WT, typename T>
 size_t narrow_smem() {
-  return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(int);
+  return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(T);
 }
 constexpr size_t kWideSmemBytes = (size_t)kSmemWarps * 3 * kSmemCap * sizeof(int);
 
@@ -1514,9 +1550,18 @@ int device_info(DeviceInfo** out) {
     e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     int rc = DIBELLA_OK;
-    if ((rc = occupancy(&D.narrow_blocks[0], (const void*)narrow_kernel<32>, kBlockThreads, narrow_smem<32>())) ||
-        (rc = occupancy(&D.narrow_blocks[1], (const void*)narrow_kernel<48>, kBlockThreads, narrow_smem<48>())) ||
-        (rc = occupancy(&D.narrow_blocks[2], (const void*)narrow_kernel<64>, kBlockThreads, narrow_smem<64>())) ||
+    if ((rc = occupancy(&D.narrow_blocks[0][0], (const void*)narrow_kernel<32, int>, kBlockThreads,
+                        narrow_smem<32, int>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][1], (const void*)narrow_kernel<48, int>, kBlockThreads,
+                        narrow_smem<48, int>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][2], (const void*)narrow_kernel<64, int>, kBlockThreads,
+                        narrow_smem<64, int>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0], (const void*)narrow_kernel<32, short>, kBlockThreads,
+                        narrow_smem<32, short>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1], (const void*)narrow_kernel<48, short>, kBlockThreads,
+                        narrow_smem<48, short>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2], (const void*)narrow_kernel<64, short>, kBlockThreads,
+                        narrow_smem<64, short>())) ||
         (rc = occupancy(&D.reg_blocks[0], (const void*)wide_reg_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.reg_blocks[1], (const void*)wide_reg_kernel<32>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[0], (const void*)wide_pk_kernel<16>, kBlockThreads, 0)) ||
@@ -1582,13 +1627,25 @@ void record(cudaStream_t st, int idx) {
   g_ev_count = idx + 1;
 }
 
-cudaError_t launch_narrow(int wt, int grid, cudaStream_t st, const ExtendParams& ep) {
-  if (wt == 32)
-    narrow_kernel<32><<<grid, kBlockThreads, narrow_smem<32>(), st>>>(ep);
-  else if (wt == 48)
-    narrow_kernel<48><<<grid, kBlockThreads, narrow_smem<48>(), st>>>(ep);
-  else
-    narrow_kernel<64><<<grid, kBlockThreads, narrow_smem<64>(), st>>>(ep);
+// int16 narrow cells (relative scores) when X allows, else int32.
+inline int narrow_kind(int xdrop) { return xdrop <= kNarrow16MaxX ? 1 : 0; }
+
+cudaError_t launch_narrow(int wt, int xdrop, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (narrow_kind(xdrop)) {
+    if (wt == 32)
+      narrow_kernel<32, short><<<grid, kBlockThreads, narrow_smem<32, short>(), st>>>(ep);
+    else if (wt == 48)
+      narrow_kernel<48, short><<<grid, kBlockThreads, narrow_smem<48, short>(), st>>>(ep);
+    else
+      narrow_kernel<64, short><<<grid, kBlockThreads, narrow_smem<64, short>(), st>>>(ep);
+  } else {
+    if (wt == 32)
+      narrow_kernel<32, int><<<grid, kBlockThreads, narrow_smem<32, int>(), st>>>(ep);
+    else if (wt == 48)
+      narrow_kernel<48, int><<<grid, kBlockThreads, narrow_smem<48, int>(), st>>>(ep);
+    else
+      narrow_kernel<64, int><<<grid, kBlockThreads, narrow_smem<64, int>(), st>>>(ep);
+  }
   return cudaGetLastError();
 }
 
@@ -1670,7 +1727,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   auto rung_queue = [&](int slots) { return kQLadder + (slots / 8 - 1); };  // 8..32 -> 3..6
   const int wt = sch.narrow_band_cap;
   const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
-  int nb = D.narrow_blocks[vi];
+  int nb = D.narrow_blocks[narrow_kind(xdrop)][vi];
   if (sch.narrow_blocks_per_sm > 0) nb = std::min(nb, sch.narrow_blocks_per_sm);
   cudaError_t e;
 
@@ -1679,7 +1736,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.narrow_q_id = kQNarrow;
   ep.esc_q = q[kQEsc1];
   ep.esc_q_id = kQEsc1;
-  if ((e = launch_narrow(wt, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
+  if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
   record(st, 2);
 
   // The configured wide form; its escalations climb the ladder.
@@ -1866,15 +1923,18 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   // extension: route it to the warp-per-extension forms, whose antidiagonal
   // latency is far lower.  Above X = 10 the narrow lanes also hand every
   // extension whose band passes the cap to the wide form, which can start only
-  // after the narrow launch ends; unless the batch gives each lane 16 or more
-  // extensions, the long ones (key above 5000) go straight to the wide form.
+  // after the narrow launch ends, so the narrow launch must not be held up by
+  // one lane's long walk: keys above 20000 (above 5000 unless the batch gives
+  // each lane 16 or more extensions) go straight to the wide form.
   // An explicit schedule is followed as given.
   if (sched == nullptr) {
     const int wt = sch.narrow_band_cap;
     const long long narrow_lanes =
-        (long long)D->sms * D->narrow_blocks[wt == 32 ? 0 : (wt == 48 ? 1 : 2)] * kBlockThreads;
+        (long long)D->sms * D->narrow_blocks[narrow_kind(scoring.xdrop)][wt == 32 ? 0 : (wt == 48 ? 1 : 2)] *
+        kBlockThreads;
     if (2 * n_pairs < 4 * narrow_lanes) sch.narrow_max_xdrop = -1;
-    else if (scoring.xdrop > 10 && 2 * n_pairs < 16 * narrow_lanes) sch.narrow_max_len = min(sch.narrow_max_len, 5000);
+    else if (scoring.xdrop > 10)
+      sch.narrow_max_len = min(sch.narrow_max_len, 2 * n_pairs < 16 * narrow_lanes ? 5000 : 20000);
   }
   record(st, 0);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,

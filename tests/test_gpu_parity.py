@@ -247,6 +247,20 @@ def test_packed_form_large_scores(c1, scoring, X):
             assert_same(got, exp, "scoring %s X=%d slots=%d lanes=%d" % (scoring, X, slots, lanes))
 
 
+@pytest.mark.parametrize("scoring,X", [((20, -20, -20), 150), ((64, -30, -64), 500), ((64, -64, -64), 8000),
+                                       ((64, -64, -64), 8001)])
+def test_narrow_form_large_scores(c1, scoring, X):
+    """The narrow form keeps int16 cells relative to a moving base for X <= 8000
+    (rebased as the best grows) and int32 cells above; scores run far beyond the
+    int16 range here."""
+    pairs = c1.pairs[:150]
+    sc = scoring + (X,)
+    exp = oracle_align(c1.reads, c1.offsets, pairs, 17, sc)
+    for cap in (32, 48, 64):
+        got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, sched=schedule(narrow_band_cap=cap, **NARROW_ALL))
+        assert_same(got, exp, "scoring %s X=%d narrow cap %d" % (scoring, X, cap))
+
+
 @pytest.mark.parametrize("name,X,n_check", [("c3_uneven", 50, 120), ("c4_repeats_small", 15, 400)])
 def test_full_batch_sampled(name, X, n_check):
     """The uneven-length (X = 50) and repeat-rich (X = 15) batches launched whole,
