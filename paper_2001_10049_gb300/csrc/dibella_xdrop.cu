@@ -832,35 +832,61 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : 1) wide_pk_kernel
   }
 }
 
-// Grouped packed form: a warp runs 32/GL extensions at once, GL lanes each,
-// chunks of 2*GL cells (same cell encoding, slots, guard and base words as the
-// packed form).  Every per-extension scalar lives in the lanes of its group, so
-// the per-antidiagonal control is computed once for all groups of the warp.
-// Slot updates are predicated per group, the jump table enters at the highest
-// slot any group needs, and the rare divergent steps (shift, activation,
-// rebase, argmax) run under a warp vote with per-group predicates.  Each group
-// pops its next extension as soon as its current one ends.
+// Grouped packed form: a warp runs NG = 32/GL extensions at once, GL lanes
+// each, chunks of 2*GL cells (same cell encoding, slots, guard and base words
+// as the packed form).  Every per-extension scalar lives in the lanes of its
+// group, so one pass of the per-antidiagonal control serves all groups.  The
+// jump table enters at the highest slot any group needs; a group whose band is
+// lower processes the extra slots too, and its band test kills them (their
+// cells lie above its hi; a slot it activates later is reset first).  Live
+// range, maximum and argmax come from per-lane masks and one full-warp
+// reduction per group.  The rare steps (window move, activation, rebase) run
+// under a warp vote with per-group predicates.  Each group pops its next
+// extension as soon as its current one ends.
+template <int NG>
+__device__ __forceinline__ int grp_reduce_max(int v, int g) {
+  int r = 0;
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    const int t = __reduce_max_sync(kFull, g == k ? v : INT32_MIN);
+    r = g == k ? t : r;
+  }
+  return r;
+}
+template <int NG>
+__device__ __forceinline__ int grp_reduce_min(int v, int g) {
+  int r = 0;
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    const int t = __reduce_min_sync(kFull, g == k ? v : INT32_MAX);
+    r = g == k ? t : r;
+  }
+  return r;
+}
+
 template <int GL, int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p) {
   static_assert(GL == 8 || GL == 16, "group of 8 or 16 lanes");
   static_assert(NC % 8 == 0 && NC >= 8 && NC <= 32, "slots come in words of 8");
   constexpr int NW = NC / 8;
+  constexpr int NG = 32 / GL;
   constexpr int CH = 2 * GL;                 // cells per chunk
   constexpr int LOG_CH = GL == 8 ? 4 : 5;
-  constexpr unsigned LOWMASK = (1u << GL) - 1u;
+  constexpr int NL = (NC + 15) / 16;
   const int lane = threadIdx.x & 31;
   const int g = lane / GL, gl = lane % GL;
-  const unsigned gmask = LOWMASK << (GL * g);
   const int src = (gl + GL - 1) & (GL - 1);
   const bool top = gl == GL - 1;
   const Scoring sc = p.sc;
   const unsigned M2 = pk_pair(sc.M, sc.M), S2 = pk_pair(sc.S, sc.S), G2 = pk_pair(sc.G, sc.G);
+  const unsigned lane2 = pk_pair(2 * gl, 2 * gl + 1);
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const uint32_t* __restrict__ words = p.words;
 
   bool active = false, exhausted = false;
   int item = 0, m = 0, n = 0, d = 0, live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
-  int cbase = 0, ctop = 0, rb = 0;
+  int cbase = 0, ctop = 0, rb = 0, bq_idx = INT32_MIN;
+  unsigned bq = 0;
   long long a_lo = 0, b_lo = 0, cells = 0;
   unsigned H[NC], Up[NC], Aw[NW], Bw[NW];
 #pragma unroll
@@ -906,6 +932,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
           cbase = -1;
           ctop = 0;
           rb = 0;
+          bq_idx = INT32_MIN;
           d = 1;
           live_lo = live_hi = 0;
           best = bi = bj = 0;
@@ -930,138 +957,139 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
     }
 
     // One antidiagonal for every active group.
-    int lo = 0, hi = -1, c0 = 0;
-    if (active) {
-      lo = max(live_lo, d - n);
-      hi = min(min(live_hi + 1, d), m);
-      c0 = lo >> LOG_CH;
-    }
-    for (;;) {  // keep slot 0 = chunk c0 - 1
-      const bool need = active && cbase < c0 - 1;
-      if (!__any_sync(kFull, need)) break;
-      if (need) {
+    int lo = max(live_lo, d - n);
+    int hi = min(min(live_hi + 1, d), m);
+    int c0 = lo >> LOG_CH;
+    int cneed = (hi + 1) >> LOG_CH;
+    const bool rare = active && ((c0 - 1 != cbase) | (cneed != ctop) | (best - rb >= kRebase));
+    if (__any_sync(kFull, rare)) {
+      for (;;) {  // keep slot 0 = chunk c0 - 1
+        const bool need = rare && cbase < c0 - 1;
+        if (!__any_sync(kFull, need)) break;
+        if (need) {
 #pragma unroll
-        for (int s = 0; s + 1 < NC; ++s) {
-          H[s] = H[s + 1];
-          Up[s] = Up[s + 1];
+          for (int s = 0; s + 1 < NC; ++s) {
+            H[s] = H[s + 1];
+            Up[s] = Up[s + 1];
+          }
+          H[NC - 1] = kNeg2;
+          Up[NC - 1] = kNeg2;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const int wn = w + 1 < NW ? w + 1 : w;
+            const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
+            Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
+            Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
+          }
+          ++cbase;
         }
-        H[NC - 1] = kNeg2;
-        Up[NC - 1] = kNeg2;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int wn = w + 1 < NW ? w + 1 : w;
-          const unsigned na = w + 1 < NW ? Aw[wn] : 0u, nb = w + 1 < NW ? Bw[wn] : 0u;
-          Aw[w] = ((Aw[w] >> 2) & 0x3FFF3FFFu) | ((na & 0x00030003u) << 14);
-          Bw[w] = ((Bw[w] >> 2) & 0x3FFF3FFFu) | ((nb & 0x00030003u) << 14);
+      }
+      if (rare && cneed - cbase > NC - 1) {  // band outgrew the slots: hand over
+        if (gl == 0) {
+          const unsigned s2 = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+          p.esc_q[s2] = item;
+          atomicAdd(&p.cnt->stat[3], 1u);
         }
-        ++cbase;
+        active = false;
       }
-    }
-    const int cneed = (hi + 1) >> LOG_CH;
-    if (active && cneed - cbase > NC - 1) {  // band outgrew the slots: hand over
-      if (gl == 0) {
-        const unsigned s2 = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-        p.esc_q[s2] = item;
-        atomicAdd(&p.cnt->stat[3], 1u);
-      }
-      active = false;
-    }
-    const bool act_new = active && cneed > ctop;
-    if (__any_sync(kFull, act_new)) {
-      if (act_new) {
-        const int snew = cneed - cbase;
-        const int i0 = CH * cneed + 2 * gl;
-        const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
-        const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
-        const int sh = 2 * (snew & 7);
-        const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
+      const bool act_new = rare && active && cneed > ctop;
+      if (__any_sync(kFull, act_new)) {
+        if (act_new) {
+          const int snew = cneed - cbase;
+          const int i0 = CH * cneed + 2 * gl;
+          const unsigned a0b = base_of(words, a_lo + i0), a1b = base_of(words, a_lo + i0 + 1);
+          const unsigned b0b = base_of(words, b_lo + 1 - d + i0), b1b = base_of(words, b_lo + 2 - d + i0);
+          const int sh = 2 * (snew & 7);
+          const unsigned clear = ~((3u << sh) | (3u << (sh + 16)));
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          if (w == (snew >> 3)) {
-            Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
-            Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+          for (int w = 0; w < NW; ++w) {
+            if (w == (snew >> 3)) {
+              Aw[w] = (Aw[w] & clear) | (a0b << sh) | (a1b << (sh + 16));
+              Bw[w] = (Bw[w] & clear) | (b0b << sh) | (b1b << (sh + 16));
+            }
+          }
+#pragma unroll
+          for (int s = 1; s < NC; ++s) {
+            if (s == snew) {
+              H[s] = kNeg2;
+              Up[s] = kNeg2;
+            }
           }
         }
+      }
+      if (rare && active) ctop = cneed;
+      const bool reb = rare && active && best - rb >= kRebase;
+      if (__any_sync(kFull, reb)) {
+        if (reb) {
+          const int delta = best - rb;
+          const unsigned dn = pk_pair(-delta, -delta);
 #pragma unroll
-        for (int s = 1; s < NC; ++s) {
-          if (s == snew) {
-            H[s] = kNeg2;
-            Up[s] = kNeg2;
+          for (int s = 0; s < NC; ++s) {
+            H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
+            Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
           }
+          rb = best;
         }
       }
     }
-    if (active) ctop = cneed;
+    if (!active) {  // an idle group computes an empty band
+      lo = 1;
+      hi = 0;
+      c0 = cbase + 1;
+    }
     const int ntop = active ? ctop - cbase : 0;
     const int ntop_w = __reduce_max_sync(kFull, ntop);
     const int wtop_w = ntop_w >> 3;
+    // Move every b base to the next cell and form the mismatch bits.
     unsigned MM[NW];
     {
-      int bfresh = 0;
-      if (active) bfresh = base_of(words, b_lo - d + CH * c0);  // lane 0 of the group, low cell of slot 1
+      const long long r = b_lo - d + CH * c0;  // lane 0 of the group, low cell of slot 1
+      if ((r >> 4) != (long long)bq_idx) {
+        bq_idx = (int)(r >> 4);
+        bq = active ? __ldg(words + (r >> 4)) : 0u;
+      }
+      const unsigned bfresh = (bq >> ((unsigned)(r & 15) * 2u)) & 3u;
       unsigned prev_top = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
         MM[w] = 0;
-        if (w <= wtop_w) {
+        if (NW == 1 || w <= wtop_w) {
           const unsigned t = __shfl_sync(kFull, Bw[w], src, GL);
           unsigned lo_new = t >> 16;
           const unsigned lo_lane0 = ((t >> 14) & 0xFFFCu) | prev_top;
           prev_top = (t >> 30) & 3u;
-          if (gl == 0) lo_new = (w == 0) ? ((lo_lane0 & ~0xCu) | ((unsigned)bfresh << 2)) : lo_lane0;
+          if (gl == 0) lo_new = (w == 0) ? ((lo_lane0 & ~0xCu) | (bfresh << 2)) : lo_lane0;
           Bw[w] = (Bw[w] << 16) | lo_new;
           const unsigned x = ~(Aw[w] ^ Bw[w]);
           MM[w] = (x | (x >> 1)) & 0x55555555u;
         }
       }
     }
-    const bool reb = active && best - rb >= kRebase;
-    if (__any_sync(kFull, reb)) {
-      if (reb) {
-        const int delta = best - rb;
-        const unsigned dn = pk_pair(-delta, -delta);
-#pragma unroll
-        for (int s = 0; s < NC; ++s) {
-          H[s] = __vmaxs2(__vadd2(H[s], dn), kNeg2);
-          Up[s] = __vmaxs2(__vadd2(Up[s], dn), kNeg2);
-        }
-        rb = best;
-      }
-    }
     const int thr_rel = best - rb - sc.X;
     const unsigned nthr2 = pk_pair(-thr_rel, -thr_rel);
-    const int rel_lo = 2 * gl - (lo - CH * cbase), rel_hi = (hi - CH * cbase) - 2 * gl;
-    const unsigned A2 = pk_pair(rel_lo, rel_lo + 1), B2 = pk_pair(rel_hi, rel_hi - 1);
-    unsigned vmax2 = kNeg2, any_slots = 0;
-    int first = INT32_MAX, last = -1;
+    const unsigned A2 = __vsub2(lane2, pk_dup(lo - CH * cbase));
+    const unsigned B2 = __vsub2(pk_dup(hi - CH * cbase), lane2);
+    unsigned vmax2 = kNeg2, lm[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) lm[q] = 0;
 #define DIBELLA_GRP_I(S) ((S) < NC ? (S) : NC - 1)
 #define DIBELLA_GRP_SLOT(S)                                                                        \
   if (S < NC) {                                                                                    \
     constexpr int s_ = DIBELLA_GRP_I(S), p_ = s_ > 0 ? s_ - 1 : 0;                                 \
-    const bool act_ = s_ <= ntop;                                                                  \
     const unsigned prevH = __shfl_sync(kFull, top ? H[p_] : H[s_], src, GL);                       \
     const unsigned u2 = __byte_perm(H[s_], prevH, 0x1076u);                                        \
-    const unsigned bits = (MM[s_ >> 3] >> (2 * (s_ & 7))) & 0x00010001u;                           \
-    const unsigned sub2 = ((bits * 0xFFFFu) & S2) | (~(bits * 0xFFFFu) & M2);                      \
+    const unsigned mis = half_sign_mask(MM[s_ >> 3] << (15 - 2 * (s_ & 7)));                       \
+    const unsigned sub2 = (mis & S2) | (~mis & M2);                                                \
     const unsigned ds = __viaddmax_s16x2(Up[s_], sub2, kNeg2);                                     \
     unsigned h2 = __viaddmax_s16x2(__vmaxs2(u2, H[s_]), G2, ds);                                   \
     const unsigned f = __vimin3_s16x2(__vadd2(h2, nthr2), __vadd2(A2, (unsigned)(CH * 0x00010001u) * s_), \
                                       __vsub2(B2, (unsigned)(CH * 0x00010001u) * s_));             \
-    const unsigned dead = ((f >> 15) & 0x00010001u) * 0xFFFFu;                                     \
+    const unsigned dead = half_sign_mask(f);                                                       \
     h2 = (h2 & ~dead) | (kNeg2 & dead);                                                            \
-    if (act_) {                                                                                    \
-      Up[s_] = u2;                                                                                 \
-      H[s_] = h2;                                                                                  \
-      vmax2 = __vmaxs2(vmax2, h2);                                                                 \
-    }                                                                                              \
-    const unsigned blo_ = (__ballot_sync(kFull, act_ && (h2 & 0xFFFFu) != 0xC000u) >> (GL * g)) & LOWMASK; \
-    const unsigned bhi_ = (__ballot_sync(kFull, act_ && (h2 >> 16) != 0xC000u) >> (GL * g)) & LOWMASK;     \
-    if (blo_ | bhi_) {                                                                             \
-      any_slots |= 1u << s_;                                                                       \
-      const int base_ = CH * (cbase + s_);                                                         \
-      first = base_ + min(blo_ ? 2 * __ffs(blo_) - 2 : CH, bhi_ ? 2 * __ffs(bhi_) - 1 : CH);      \
-      if (last < 0) last = base_ + max(blo_ ? 2 * (31 - __clz(blo_)) : -1, bhi_ ? 2 * (31 - __clz(bhi_)) + 1 : -1); \
-    }                                                                                              \
+    Up[s_] = u2;                                                                                   \
+    H[s_] = h2;                                                                                    \
+    vmax2 = __vmaxs2(vmax2, h2);                                                                   \
+    lm[s_ >> 4] |= ~dead & (0x00010001u << (s_ & 15));                                             \
   }
     switch (ntop_w) {
       case 31: DIBELLA_GRP_SLOT(31) [[fallthrough]];
@@ -1101,43 +1129,66 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
 #undef DIBELLA_GRP_I
     H[0] = kNeg2;
     if (active) cells += hi - lo + 1;
-    const int vrel = __reduce_max_sync(gmask, max(pk_lo(vmax2), pk_hi(vmax2)));
-    const bool improved = active && any_slots != 0 && vrel + rb > best;
+    // Lowest and highest live cell of the lane (relative to chunk cbase), then
+    // of the group.
+    int my_first = INT32_MAX, my_last = -1;
+#pragma unroll
+    for (int q = NL - 1; q >= 0; --q) {
+      const unsigned comb = (lm[q] | (lm[q] >> 16)) & 0xFFFFu;
+      if (comb) {
+        const int s_lo = __ffs(comb) - 1;
+        my_first = CH * (16 * q + s_lo) + 2 * gl + (int)(((lm[q] >> s_lo) & 1u) ^ 1u);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const unsigned comb = (lm[q] | (lm[q] >> 16)) & 0xFFFFu;
+      if (comb) {
+        const int s_hi = 31 - __clz(comb);
+        my_last = CH * (16 * q + s_hi) + 2 * gl + (int)((lm[q] >> (16 + s_hi)) & 1u);
+      }
+    }
+    const int last_rel = grp_reduce_max<NG>(my_last, g);
+    const int first_rel = grp_reduce_min<NG>(my_first, g);
+    const int vrel = grp_reduce_max<NG>(max(pk_lo(vmax2), pk_hi(vmax2)), g);
+    const bool improved = active && last_rel >= 0 && vrel + rb > best;
     if (__any_sync(kFull, improved)) {
-      const int sl = any_slots ? __ffs(any_slots) - 1 : NC, sh = any_slots ? 31 - __clz(any_slots) : 0;
-      const int sh_w = __reduce_max_sync(kFull, improved ? sh : 0);
+      // Smallest i holding the new best: each lane's first match over the
+      // group's live slots, then the group minimum.
+      const int sl = improved ? first_rel >> LOG_CH : NC, sh = improved ? last_rel >> LOG_CH : 0;
+      const int sh_w = __reduce_max_sync(kFull, sh);
       const unsigned v2 = pk_pair(vrel, vrel);
-      int cand = INT32_MAX;
+      int my_c = INT32_MAX;
 #pragma unroll
       for (int s = 1; s < NC; ++s) {
         if (s > sh_w) break;
-        const bool in = improved && s >= sl && s <= sh;
-        const unsigned e = H[s] ^ v2;
-        const unsigned blo = (__ballot_sync(kFull, in && (e & 0xFFFFu) == 0) >> (GL * g)) & LOWMASK;
-        const unsigned bhi = (__ballot_sync(kFull, in && (e >> 16) == 0) >> (GL * g)) & LOWMASK;
-        const int f0 = blo ? 2 * (__ffs(blo) - 1) : INT32_MAX;
-        const int f1 = bhi ? 2 * (__ffs(bhi) - 1) + 1 : INT32_MAX;
-        if (min(f0, f1) != INT32_MAX) cand = min(cand, CH * (cbase + s) + min(f0, f1));
+        if (s >= sl && s <= sh && my_c == INT32_MAX) {
+          const unsigned e = H[s] ^ v2;
+          if ((e & 0xFFFFu) == 0) my_c = CH * s + 2 * gl;
+          else if ((e >> 16) == 0) my_c = CH * s + 2 * gl + 1;
+        }
       }
+      const int cand = grp_reduce_min<NG>(my_c, g);
       if (improved) {
         best = vrel + rb;
-        bi = cand;
-        bj = d - cand;
+        bi = CH * cbase + cand;
+        bj = d - bi;
       }
     }
-    const bool finished = active && (any_slots == 0 || d == m + n);
-    if (finished) {
-      if (gl == 0) {
-        ExtOut o;
-        o.best = best; o.i_end = bi; o.j_end = bj; o.status = 0; o.cells = cells;
-        p.ext[item] = o;
-        atomicAdd(&p.cnt->cells[1], (unsigned long long)cells);
+    if (active) {
+      if (last_rel < 0 || d == m + n) {
+        if (gl == 0) {
+          ExtOut o;
+          o.best = best; o.i_end = bi; o.j_end = bj; o.status = 0; o.cells = cells;
+          p.ext[item] = o;
+          atomicAdd(&p.cnt->cells[1], (unsigned long long)cells);
+        }
+        active = false;
+      } else {
+        live_lo = CH * cbase + first_rel;
+        live_hi = CH * cbase + last_rel;
+        ++d;
       }
-      active = false;
-    } else if (active) {
-      live_lo = first;
-      live_hi = last;
-      ++d;
     }
   }
 }
