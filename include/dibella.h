@@ -128,15 +128,16 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  *           else 32 int32 cells of one warp;
  * an extension whose band outgrows its form is re-run from the start by the
  * next wider form: the narrow form's by the wide form, the wide form's by
- * the next rung of 8 -> 16 -> 24 -> 32 slots, then by a warp with a
- * 4096-cell shared-memory band, and beyond that by a warp whose band lives
- * in the workspace (sized by max_read_len: it cannot overflow).
+ * the next rung of 8 -> 16 -> 24 -> 32 slots, then by a block of 8 warps
+ * per extension with an 8192-cell band in shared memory (the CTA form), and
+ * beyond that by a warp whose band lives in the workspace (sized by
+ * max_read_len: it cannot overflow).
  * An extension is routed to narrow when xdrop <= narrow_max_xdrop and
  * min(remaining A, remaining B) <= narrow_max_len.  When a call passes no
- * schedule, batches with fewer than 4 extensions per resident narrow lane go
- * entirely to the wide form (they would wait on one lane's longest
+ * schedule, batches with fewer than 1.5 extensions per resident narrow lane
+ * go entirely to the wide form (they would wait on one lane's longest
  * extension), and for xdrop > 10 keys above 20000 (above 5000 in batches
- * with fewer than 16 extensions per lane) go to the wide form (a narrow lane
+ * with fewer than 7 extensions per lane) go to the wide form (a narrow lane
  * would otherwise hold up the escalations behind its long extension); an
  * explicit schedule is followed as given.  Work is ordered by
  * n_buckets length buckets (longest first); bucket b holds keys below
@@ -302,18 +303,18 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
  * stream capture they are recorded as external events, so a replayed CUDA
  * graph records them too.  dibella_phase_times() synchronises on the last
  * event and writes up to n_max phase durations in ms: queueing (expand, scan,
- * scatter), wide register form, narrow form, escalations (shared-memory and
- * global forms), combine; returns the count written.  Enable it before any
- * capture (it creates the events). */
+ * scatter), narrow form, wide form, escalations (the narrow escalations, the
+ * slot ladder, the CTA and global forms), combine; returns the count
+ * written.  Enable it before any capture (it creates the events). */
 int dibella_enable_phase_timing(int enable);
 int dibella_phase_times(float* ms_out, int n_max);
 
 /* Counters of the last batch run with `workspace` (synchronises `stream`):
  * out[0] extensions routed narrow, out[1] routed wide, out[2..4] extensions
- * that outgrew the narrow / wide / shared-memory form, out[5] band
+ * that outgrew the narrow / wide / CTA (shared-memory) form, out[5] band
  * overflows, out[6..9] evaluated cells of the extensions finished by the
- * narrow, wide (register or packed), shared-memory and global-band forms.  Returns the number
- * written (<= n_max, at most 10), or a negative status. */
+ * narrow, wide (register or packed), CTA and global-band forms.  Returns the
+ * number written (<= n_max, at most 10), or a negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */

@@ -1193,29 +1193,157 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
   }
 }
 
-// Shared-memory form, one warp per extension, band of kSmemCap cells.
-constexpr int kSmemCap = 4096;
-constexpr int kSmemWarps = 2;
-__global__ void __launch_bounds__(kSmemWarps * 32) wide_smem_kernel(ExtendParams p) {
-  extern __shared__ int smem[];
-  const int lane = threadIdx.x & 31;
-  int* arr = smem + (threadIdx.x >> 5) * 3 * kSmemCap;
+// CTA form: one CTA of kCtaWarps warps per extension, for the widest bands.
+// Three antidiagonals of kCtaCap int32 cells in a circular shared-memory array
+// (cell i at i mod kCtaCap, as in the warp form); the band's 32-cell chunks
+// are dealt round-robin to the warps.  Per antidiagonal each warp reduces its
+// own maximum and live range, and one barrier publishes them (double-buffered
+// by antidiagonal parity, so the next antidiagonal's writes cannot overtake a
+// slow reader); every thread then combines the kCtaWarps entries itself, so
+// all threads hold the same band, best and threshold.  The argmax, needed
+// only when the best improves, takes one more barrier.
+constexpr int kCtaWarps = 8;
+constexpr int kCtaThreads = kCtaWarps * 32;
+constexpr int kCtaCap = 8192;
+struct CtaShared {
+  int red[2][kCtaWarps][3];  // per warp: max, first live, last live
+  int arg[kCtaWarps];        // per warp: smallest i holding the new best
+  int item;
+};
+constexpr size_t kCtaSmemBytes = sizeof(CtaShared) + (size_t)3 * kCtaCap * sizeof(int);
+
+// Returns false (uniformly across the CTA) when the band outgrew kCtaCap - 3.
+__device__ bool extend_cta(const uint32_t* __restrict__ words, const Item& it, const Scoring sc,
+                           CtaShared& sh, int* arr, ExtOut* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int mask = kCtaCap - 1;
+  int* H2 = arr;
+  int* H1 = arr + kCtaCap;
+  int* H0 = arr + 2 * kCtaCap;
+  const int m = it.m, n = it.n;
+  if (threadIdx.x == 0) {
+    H1[0] = 0;
+    H1[mask] = kNeg;
+    H1[1] = kNeg;
+    H2[mask] = kNeg;
+    H2[0] = kNeg;
+  }
+  __syncthreads();
+  int live_lo = 0, live_hi = 0, best = 0, bi = 0, bj = 0;
+  long long cells = 0;
+  bool ok = true;
+  for (int d = 1; d <= m + n; ++d) {
+    const int lo = max(live_lo, d - n);
+    const int hi = min(min(live_hi + 1, d), m);
+    if (hi - lo + 3 > kCtaCap) {
+      ok = false;
+      break;
+    }
+    const int thr = best - sc.X;
+    const long long abase = it.a0 - 1, bbase = it.b0 + 1 - d;
+    int vmax = kNeg, first = INT32_MAX, last = -1;
+    for (int i0 = lo + 32 * warp; i0 <= hi; i0 += 32 * kCtaWarps) {
+      const int i = i0 + lane;
+      int h = kNeg;
+      if (i <= hi) {
+        const int lf = H1[i & mask];
+        const int u = H1[(i - 1) & mask];
+        const int dg = H2[(i - 1) & mask];
+        const int ca = base_at(words, abase + i), cb = base_at(words, bbase + i);
+        const int sub = (ca ^ cb) == 3 ? sc.M : sc.S;
+        h = max(max(u, lf) + sc.G, dg + sub);
+        h = h >= thr ? h : kNeg;
+        H0[i & mask] = h;
+      }
+      vmax = max(vmax, h);
+      const unsigned bl = __ballot_sync(kFull, h != kNeg);
+      if (bl) {
+        if (first == INT32_MAX) first = i0 + __ffs(bl) - 1;
+        last = i0 + 31 - __clz(bl);
+      }
+    }
+    vmax = __reduce_max_sync(kFull, vmax);
+    const int par = d & 1;
+    if (lane == 0) {
+      sh.red[par][warp][0] = vmax;
+      sh.red[par][warp][1] = first;
+      sh.red[par][warp][2] = last;
+    }
+    if (threadIdx.x == 0) H0[(lo - 1) & mask] = kNeg;
+    if (threadIdx.x == 1) H0[(hi + 1) & mask] = kNeg;
+    __syncthreads();
+    int cmax = kNeg, cfirst = INT32_MAX, clast = -1;
+#pragma unroll
+    for (int w = 0; w < kCtaWarps; ++w) {
+      cmax = max(cmax, sh.red[par][w][0]);
+      cfirst = min(cfirst, sh.red[par][w][1]);
+      clast = max(clast, sh.red[par][w][2]);
+    }
+    cells += hi - lo + 1;
+    if (cmax == kNeg) break;
+    if (cmax > best) {
+      int cand = INT32_MAX;
+      for (int i0 = lo + 32 * warp; i0 <= clast; i0 += 32 * kCtaWarps) {
+        if (i0 + 31 < cfirst) continue;
+        const int i = i0 + lane;
+        const unsigned bl = __ballot_sync(kFull, i >= cfirst && i <= clast && H0[i & mask] == cmax);
+        if (bl) {
+          cand = i0 + __ffs(bl) - 1;
+          break;
+        }
+      }
+      if (lane == 0) sh.arg[warp] = cand;
+      __syncthreads();
+      int c = INT32_MAX;
+#pragma unroll
+      for (int w = 0; w < kCtaWarps; ++w) c = min(c, sh.arg[w]);
+      best = cmax;
+      bi = c;
+      bj = d - c;
+      __syncthreads();  // sh.arg is read before any warp can write it again
+    }
+    live_lo = cfirst;
+    live_hi = clast;
+    int* t = H2;
+    H2 = H1;
+    H1 = H0;
+    H0 = t;
+  }
+  if (ok && threadIdx.x == 0) {
+    out->best = best;
+    out->i_end = bi;
+    out->j_end = bj;
+    out->status = 0;
+    out->cells = cells;
+  }
+  __syncthreads();
+  return ok;
+}
+
+__global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
+  extern __shared__ int smem_cta[];
+  CtaShared& sh = *reinterpret_cast<CtaShared*>(smem_cta);
+  int* arr = smem_cta + sizeof(CtaShared) / sizeof(int);
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   for (;;) {
-    const unsigned q = pop_warp(p.cnt, p.wide_q_id);
-    if (q >= tail) break;
-    const int item = p.wide_q[q];
+    if (threadIdx.x == 0) {
+      const unsigned q = atomicAdd(&p.cnt->head[p.wide_q_id], 1u);
+      sh.item = q < tail ? p.wide_q[q] : -1;
+    }
+    __syncthreads();
+    const int item = sh.item;
+    __syncthreads();  // every thread has read sh.item before thread 0 may rewrite it
+    if (item < 0) break;
     const Item it = p.items[item];
-    if (!extend_warp<false>(p.words, it, p.sc, arr, kSmemCap, p.ext + item)) {
-      if (lane == 0) {
+    if (!extend_cta(p.words, it, p.sc, sh, arr, p.ext + item)) {
+      if (threadIdx.x == 0) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
         p.esc_q[s] = item;
         atomicAdd(&p.cnt->stat[4], 1u);
       }
-    } else if (lane == 0) {
+    } else if (threadIdx.x == 0) {
       atomicAdd(&p.cnt->cells[2], (unsigned long long)p.ext[item].cells);
     }
-    __syncwarp();
   }
 }
 
@@ -1520,7 +1648,7 @@ struct DeviceInfo {
   int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
   int grp16_blocks[3] = {0, 0, 0};   // wide_grp_kernel<16, 16/24/32> blocks per SM
   int grp8_blocks[2] = {0, 0};       // wide_grp_kernel<8, 16/24> blocks per SM
-  int smem_blocks = 0;               // wide_smem_kernel blocks per SM
+  int cta_blocks = 0;                // wide_cta_kernel blocks per SM
 };
 std::mutex g_dev_mu;
 DeviceInfo g_dev[64];
@@ -1577,7 +1705,6 @@ template <int WT, typename T>
 size_t narrow_smem() {
   return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(T);
 }
-constexpr size_t kWideSmemBytes = (size_t)kSmemWarps * 3 * kSmemCap * sizeof(int);
 
 int occupancy(int* out, const void* fn, int threads, size_t smem) {
   if (smem > 48 * 1024) {
@@ -1624,7 +1751,7 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.grp16_blocks[2], (const void*)wide_grp_kernel<16, 32>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.grp8_blocks[0], (const void*)wide_grp_kernel<8, 16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.grp8_blocks[1], (const void*)wide_grp_kernel<8, 24>, kBlockThreads, 0)) ||
-        (rc = occupancy(&D.smem_blocks, (const void*)wide_smem_kernel, kSmemWarps * 32, kWideSmemBytes)))
+        (rc = occupancy(&D.cta_blocks, (const void*)wide_cta_kernel, kCtaThreads, kCtaSmemBytes)))
       return rc;
     D.ready = true;
   }
@@ -1819,8 +1946,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wide_q_id = kQSmem;
   ep.esc_q = q[kQGlobal];
   ep.esc_q_id = kQGlobal;
-  wide_smem_kernel<<<D.sms * D.smem_blocks, kSmemWarps * 32, kWideSmemBytes, st>>>(ep);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_smem launch");
+  wide_cta_kernel<<<D.sms * D.cta_blocks, kCtaThreads, kCtaSmemBytes, st>>>(ep);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_cta launch");
 
   ep.wide_q = q[kQGlobal];
   ep.wide_q_id = kQGlobal;
@@ -1969,23 +2096,24 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   char* ws = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // With the default schedule, a batch too small to give every resident narrow
-  // lane a few extensions would be bound by one lane's walk through its longest
-  // extension: route it to the warp-per-extension forms, whose antidiagonal
-  // latency is far lower.  Above X = 10 the narrow lanes also hand every
-  // extension whose band passes the cap to the wide form, which can start only
-  // after the narrow launch ends, so the narrow launch must not be held up by
-  // one lane's long walk: keys above 20000 (above 5000 unless the batch gives
-  // each lane 16 or more extensions) go straight to the wide form.
-  // An explicit schedule is followed as given.
+  // With the default schedule, a batch too small to give the resident narrow
+  // lanes about one and a half extensions each would occupy few warps on few
+  // SMs and be bound by one lane's walk through its longest extension: route it
+  // to the warp-per-extension forms, whose antidiagonal latency is far lower.
+  // Above X = 10 the narrow lanes also hand every extension whose band passes
+  // the cap to the wide form, which can start only after the narrow launch
+  // ends, so the narrow launch must not be held up by one lane's long walk:
+  // keys above 20000 (above 5000 unless the batch gives each lane 7 or more
+  // extensions) go straight to the wide form.  An explicit schedule is
+  // followed as given.
   if (sched == nullptr) {
     const int wt = sch.narrow_band_cap;
     const long long narrow_lanes =
         (long long)D->sms * D->narrow_blocks[narrow_kind(scoring.xdrop)][wt == 32 ? 0 : (wt == 48 ? 1 : 2)] *
         kBlockThreads;
-    if (2 * n_pairs < 4 * narrow_lanes) sch.narrow_max_xdrop = -1;
+    if (2 * 2 * n_pairs < 3 * narrow_lanes) sch.narrow_max_xdrop = -1;
     else if (scoring.xdrop > 10)
-      sch.narrow_max_len = min(sch.narrow_max_len, 2 * n_pairs < 16 * narrow_lanes ? 5000 : 20000);
+      sch.narrow_max_len = min(sch.narrow_max_len, 2 * n_pairs < 7 * narrow_lanes ? 5000 : 20000);
   }
   record(st, 0);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,

@@ -115,12 +115,13 @@ def test_fuzz_medium(scoring):
 
 
 @pytest.mark.parametrize("lengths,counter", [((900, 1300), "escalated_wide"),
-                                              ((4300, 4800), "escalated_smem")])
+                                              ((4300, 4800), "cells_smem"),
+                                              ((8400, 8800), "escalated_smem")])
 def test_infinite_x_escalations(lengths, counter):
     """X = infinity: the band is the whole matrix (and X is above the packed
     form's limit, so the int32 register form runs).  Extensions wider than its
-    band go to the shared-memory form, and wider than 4096 cells to the
-    global-memory form."""
+    band go to the CTA form (one block per extension, band in shared memory),
+    and wider than 8189 cells to the global-memory form."""
     import paper_2001_10049_gb300 as dib
     rng = random.Random(lengths[0])
     reads = random_overlap_reads(rng, 5, lengths[0], lengths[1], 0.1)
