@@ -101,6 +101,10 @@ struct ExtendParams {
   int narrow_q_id;
   int* esc_q;         // where extensions that outgrow the form go
   int esc_q_id;
+  // A slot-ladder rung whose queue holds at most this many extensions passes
+  // them all on to esc_q unextended: so few are latency bound, and the CTA
+  // form above the ladder walks a wide band faster than one warp (0 = never).
+  unsigned forward_max;
   Scoring sc;
   int* gband;
   int gcap;
@@ -788,10 +792,16 @@ template <int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  const bool fwd = tail <= p.forward_max;
   for (;;) {
     const unsigned q = pop_warp(p.cnt, p.wide_q_id);
     if (q >= tail) break;
     const int item = p.wide_q[q];
+    if (fwd) {
+      if (lane == 0) p.esc_q[atomicAdd(&p.cnt->tail[p.esc_q_id], 1u)] = item;
+      __syncwarp();
+      continue;
+    }
     const Item it = p.items[item];
     if (!extend_reg<NC>(p.words, it, p.sc, p.ext + item)) {
       if (lane == 0) {
@@ -807,17 +817,25 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
 }
 
 // Packed form, one warp per extension (routed here only when X <= kPackedMaxX).
-// The 8-slot form asks for 9 resident CTAs per SM: measured a little faster than
-// the unconstrained allocation (8 CTAs) and than 10 or 12 (the slot code then
-// recomputes values it can no longer keep in registers).
+// Resident CTAs per SM asked of the compiler, by measurement: 9 for 8 slots (a
+// little faster than the unconstrained 8, and than 10 or 12, where the slot
+// code recomputes values it can no longer keep in registers), 6 for 16 slots,
+// 4 for 24 slots (c3: 14% faster than the unconstrained 3, without spills).
 template <int NC>
-__global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : 1) wide_pk_kernel(ExtendParams p) {
+__global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (NC == 24 ? 4 : 1)))
+    wide_pk_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
+  const bool fwd = NC > 8 && tail <= p.forward_max;  // 8 slots is never a ladder rung
   for (;;) {
     const unsigned q = pop_warp(p.cnt, p.wide_q_id);
     if (q >= tail) break;
     const int item = p.wide_q[q];
+    if (fwd) {
+      if (lane == 0) p.esc_q[atomicAdd(&p.cnt->tail[p.esc_q_id], 1u)] = item;
+      __syncwarp();
+      continue;
+    }
     const Item it = p.items[item];
     if (!extend_pk<NC>(p.words, it, p.sc, p.ext + item)) {
       if (lane == 0) {
@@ -1934,6 +1952,9 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     up.wide_slots = rungs[r];
     up.wide_group_lanes = 32;
     const int next_q = r + 1 < n_rungs ? rung_queue(rungs[r]) : kQSmem;
+    // Only the top rung hands a short queue straight to the CTA form (the
+    // lower rungs' extensions mostly fit the next rung; measured).
+    ep.forward_max = r + 1 == n_rungs ? (unsigned)(4 * D.sms * D.cta_blocks) : 0u;
     ep.wide_q = q[cur_q];
     ep.wide_q_id = cur_q;
     ep.esc_q = q[next_q];
@@ -1941,6 +1962,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     if ((e = launch_wide(D, up, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (ladder)");
     cur_q = next_q;
   }
+  ep.forward_max = 0;
 
   ep.wide_q = q[kQSmem];
   ep.wide_q_id = kQSmem;
@@ -2130,6 +2152,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.sc = {scoring.match, scoring.mismatch, scoring.gap, scoring.xdrop};
   ep.gband = (int*)(ws + L.gband);
   ep.gcap = gcap;
+  ep.forward_max = 0;
   int* q[kNumQ];
   for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
