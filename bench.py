@@ -97,6 +97,19 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from a one-pass ncu capture of this bench's default
+# command (profiles/ names the file and the command).  Keyed by workload, X and
+# launch; valid only for the default schedule and the kernels it was taken on.
+NCU_TRAFFIC = {}
+
+
+def traffic_for(workload, args, X, launch):
+    if args.schedule or args.sample_pairs:
+        return None
+    return NCU_TRAFFIC.get((workload, X, launch))
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -450,9 +463,11 @@ def main():
     # First calls outside capture (device set-up), then one graph per X.
     graphs = {}
     counters = {}
+    launches = {}
     with torch.cuda.stream(stream):
         for X in XD:
             al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
+            launches[X] = dib.dibella_last_launch_count()
             torch.cuda.synchronize(dev)
             counters[X] = dib.dibella_batch_counters(al.workspace, stream=stream)
         for X in XD:
@@ -542,16 +557,26 @@ def main():
         return
     pk, pk_kind = peaks()
     clk = clocks.summary()
-    # Roofline of the dominant kernel (the first extend launch): integer ops of
-    # the cells it finished / its event-timed duration, per launch.
-    # phases: 0 queueing, 1 narrow form, 2 wide form, 3 escalations, 4 combine
-    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 5]), axis=0) for X in XD}
+    # Roofline of the dominant kernel: integer ops of the cells its launch
+    # finished / that launch's duration, from the phase events recorded on the
+    # launching stream inside every replayed graph of the timed region.
+    # phases: 0 queueing, 1 narrow form, 2 first wide launch, 3 wide launch on
+    # the narrow escalations, 4 slot ladder + CTA + global forms, 5 combine
+    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 6]), axis=0) for X in XD}
     batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XD}
-    # dominant kernel per X: the longer of the register and narrow launches
-    dom = {X: ("wide", 2, "cells_wide") if phase[X][2] >= phase[X][1] else ("narrow", 1, "cells_narrow")
-           for X in XD}
-    ext_ms = {X: float(phase[X][dom[X][1]]) for X in XD}
-    achieved = float(np.mean([OPS_PER_CELL * counters[X][dom[X][2]] / (ext_ms[X] * 1e-3) / 1e12 for X in XD]))
+    launch_cells = {X: {"narrow form": (1, counters[X]["cells_narrow"]),
+                        "wide form, first launch": (2, counters[X]["cells_wide"] - counters[X]["cells_wide_esc"]
+                                                     - counters[X]["cells_ladder"]),
+                        "wide form on the narrow escalations": (3, counters[X]["cells_wide_esc"])}
+                    for X in XD}
+    per_launch = {X: {name: {"ms": float(phase[X][i]), "cells": int(c),
+                             "tops": OPS_PER_CELL * c / (phase[X][i] * 1e-3) / 1e12 if phase[X][i] > 0 else 0.0}
+                      for name, (i, c) in launch_cells[X].items()} for X in XD}
+    # the dominant launch of the whole step: the longest of them over all X
+    domX, domName = max(((X, name) for X in XD for name in per_launch[X]), key=lambda t: per_launch[t[0]][t[1]]["ms"])
+    dom_rec = per_launch[domX][domName]
+    dom = {X: max(per_launch[X], key=lambda nm: per_launch[X][nm]["ms"]) for X in XD}
+    achieved = dom_rec["tops"]
     peak_ops = SM_COUNT * INT32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     total_cells = sum(cells.values())
     value = world * len(XD) * n_cand / (my_ms * 1e-3)
@@ -580,17 +605,21 @@ def main():
         "per_xdrop": {str(X): {"ms": batch_ms[X], "pairs_per_s": n_cand / (batch_ms[X] * 1e-3),
                                "gcups": cells[X] / (batch_ms[X] * 1e-3) / 1e9, "cells": cells[X],
                                "phase_ms": [round(float(v), 3) for v in phase[X]],
-                               "dominant": dom[X][0], "counters": counters[X]} for X in XD},
+                               "dominant": dom[X], "launches": {k: {"ms": round(v["ms"], 3), "cells": v["cells"],
+                                                                    "tops": round(v["tops"], 4)}
+                                                                for k, v in per_launch[X].items()},
+                               "counters": counters[X]} for X in XD},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": ", ".join("X=%d: %s form" % (X, dom[X][0]) for X in XD),
+                     "frac": achieved / peak_ops, "traffic": traffic_for(w.name, args, domX, domName),
+                     "kernel": "%s (X=%d), %d cells in %.1f ms per launch" % (domName, domX, dom_rec["cells"],
+                                                                            dom_rec["ms"]),
                      "peak_source": "%d SMs x %d INT32 lanes x %.0f MHz (%s sm_max_mhz)"
                                     % (SM_COUNT, INT32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), pk_kind),
                      "ops_per_cell": OPS_PER_CELL},
         "e2e": ({"value": world * len(XD) * n_cand / (e2e_step * 1e-3), "unit": "aligned pairs/s",
                  "h2d_bytes_per_step": len(XD) * n_seeds * 24, "d2h_bytes_per_step": len(XD) * n_seeds * 40}
                 if e2e_step else None),
-        "gpu_launches": args.steps * len(XD) * 8,
+        "gpu_launches": args.steps * sum(launches[X] for X in XD),
         "clocks": clk,
         "plain_per_pair": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,

@@ -303,9 +303,10 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
  * stream capture they are recorded as external events, so a replayed CUDA
  * graph records them too.  dibella_phase_times() synchronises on the last
  * event and writes up to n_max phase durations in ms: queueing (expand, scan,
- * scatter), narrow form, wide form, escalations (the narrow escalations, the
- * slot ladder, the CTA and global forms), combine; returns the count
- * written.  Enable it before any capture (it creates the events). */
+ * scatter), narrow form, first wide launch, the wide launch on the narrow
+ * escalations, the slot ladder with the CTA and global forms, combine;
+ * returns the count written (6 after a batch).  Enable it before any capture
+ * (it creates the events). */
 int dibella_enable_phase_timing(int enable);
 int dibella_phase_times(float* ms_out, int n_max);
 
@@ -313,9 +314,17 @@ int dibella_phase_times(float* ms_out, int n_max);
  * out[0] extensions routed narrow, out[1] routed wide, out[2..4] extensions
  * that outgrew the narrow / wide / CTA (shared-memory) form, out[5] band
  * overflows, out[6..9] evaluated cells of the extensions finished by the
- * narrow, wide (register or packed), CTA and global-band forms.  Returns the
- * number written (<= n_max, at most 10), or a negative status. */
+ * narrow, wide (register or packed, all launches), CTA and global-band
+ * forms, out[10] and out[11] the part of out[7] finished by the wide launch
+ * on the narrow escalations and by the slot-ladder rungs.  Returns the
+ * number written (<= n_max, at most 12), or a negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
+
+/* Number of kernels the calling thread's last dibella_xdrop_batch (or _host /
+ * _noalloc) launched: queueing, every extension form (launched even when its
+ * queue is empty) and combine.  Host-side count; no device work, no errors.
+ * The paper has no counterpart: it reports the GPU work of a batch. */
+int dibella_last_launch_count(void);
 
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char* dibella_last_error(void);

@@ -114,6 +114,7 @@ def _lib():
             "dibella_enable_phase_timing": ([ctypes.c_int], i32),
             "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
             "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
+            "dibella_last_launch_count": ([], i32),
             "dibella_last_error": ([], ctypes.c_char_p),
             "dibella_version": ([], ctypes.c_char_p),
         }
@@ -296,13 +297,17 @@ def dibella_phase_times(n_max: int = 8) -> list[float]:
 
 
 def dibella_batch_counters(workspace, stream=None) -> dict:
-    buf = (ctypes.c_int64 * 10)()
-    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 10)
+    buf = (ctypes.c_int64 * 12)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 12)
     if n < 0:
         _check(n, "dibella_batch_counters")
     keys = ["narrow", "wide", "escalated_narrow", "escalated_wide", "escalated_smem", "band_overflow",
-            "cells_narrow", "cells_wide", "cells_smem", "cells_global"]
+            "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder"]
     return {keys[i]: int(buf[i]) for i in range(n)}
+
+
+def dibella_last_launch_count() -> int:
+    return int(_lib().dibella_last_launch_count())
 
 
 def dibella_last_error() -> str:

@@ -81,7 +81,9 @@ struct Counters {
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
   unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / wide /
                           // shared-memory form, band overflows
-  unsigned long long cells[4];  // cells of finished extensions: narrow, wide pass 1, wide pass 2, global
+  // cells of finished extensions: 0 narrow, 1 wide (first launch), 2 CTA,
+  // 3 global, 4 wide launch on the narrow escalations, 5 slot-ladder rungs
+  unsigned long long cells[6];
 };
 
 
@@ -105,6 +107,7 @@ struct ExtendParams {
   // them all on to esc_q unextended: so few are latency bound, and the CTA
   // form above the ladder walks a wide band faster than one warp (0 = never).
   unsigned forward_max;
+  int cells_idx;  // Counters::cells entry the wide forms add to
   Scoring sc;
   int* gband;
   int gcap;
@@ -810,7 +813,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
         atomicAdd(&p.cnt->stat[3], 1u);
       }
     } else if (lane == 0) {
-      atomicAdd(&p.cnt->cells[1], (unsigned long long)p.ext[item].cells);
+      atomicAdd(&p.cnt->cells[p.cells_idx], (unsigned long long)p.ext[item].cells);
     }
     __syncwarp();
   }
@@ -844,7 +847,7 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
         atomicAdd(&p.cnt->stat[3], 1u);
       }
     } else if (lane == 0) {
-      atomicAdd(&p.cnt->cells[1], (unsigned long long)p.ext[item].cells);
+      atomicAdd(&p.cnt->cells[p.cells_idx], (unsigned long long)p.ext[item].cells);
     }
     __syncwarp();
   }
@@ -1199,7 +1202,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
           ExtOut o;
           o.best = best; o.i_end = bi; o.j_end = bj; o.status = 0; o.cells = cells;
           p.ext[item] = o;
-          atomicAdd(&p.cnt->cells[1], (unsigned long long)cells);
+          atomicAdd(&p.cnt->cells[p.cells_idx], (unsigned long long)cells);
         }
         active = false;
       } else {
@@ -1673,6 +1676,7 @@ DeviceInfo g_dev[64];
 
 bool g_timing = false;
 cudaEvent_t g_ev[8] = {};
+thread_local int g_launches = 0;  // kernel launches of this thread's last batch
 int g_ev_count = 0;
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -1842,6 +1846,7 @@ cudaError_t launch_narrow(int wt, int xdrop, int grid, cudaStream_t st, const Ex
     else
       narrow_kernel<64, int><<<grid, kBlockThreads, narrow_smem<64, int>(), st>>>(ep);
   }
+  ++g_launches;
   return cudaGetLastError();
 }
 
@@ -1895,6 +1900,7 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
     else
       wide_grp_kernel<8, 24><<<grid, kBlockThreads, 0, st>>>(ep);
   }
+  ++g_launches;
   return cudaGetLastError();
 }
 
@@ -1902,10 +1908,13 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
 //   narrow form        on Narrow        (outgrown -> Esc1)
 //   wide form (S slots) on Wide, Esc1   (outgrown -> ladder queue of S)
 //   wide form, next rung of the slot ladder 8 -> 16 -> 24 -> 32, on the queue
-//                      of the rung below (outgrown -> its own queue)
-//   shared-memory form on Smem          (outgrown -> Global)
+//                      of the rung below (outgrown -> its own queue; the top
+//                      rung hands a short queue on unextended)
+//   CTA form           on Smem          (outgrown -> Global)
 //   global form        on Global
-// Every launch whose queue is empty returns at once.
+// Every launch whose queue is empty returns at once.  Phase events: 2 after
+// the narrow launch, 3 after the first wide launch, 4 after the wide launch
+// on the narrow escalations, 5 after the ladder, CTA and global launches.
 int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, ExtendParams ep,
                       int* const q[kNumQ], cudaStream_t st) {
   dibella_schedule_t sch = sch_in;
@@ -1942,11 +1951,15 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.esc_q_id = cur_q;
   ep.wide_q = q[kQWide];
   ep.wide_q_id = kQWide;
+  ep.cells_idx = 1;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
   record(st, 3);
   ep.wide_q = q[kQEsc1];
   ep.wide_q_id = kQEsc1;
+  ep.cells_idx = 4;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
+  record(st, 4);
+  ep.cells_idx = 5;
   for (int r = 0; r < n_rungs; ++r) {
     dibella_schedule_t up = sch;
     up.wide_slots = rungs[r];
@@ -1969,13 +1982,15 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.esc_q = q[kQGlobal];
   ep.esc_q_id = kQGlobal;
   wide_cta_kernel<<<D.sms * D.cta_blocks, kCtaThreads, kCtaSmemBytes, st>>>(ep);
+  ++g_launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "wide_cta launch");
 
   ep.wide_q = q[kQGlobal];
   ep.wide_q_id = kQGlobal;
   global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
+  ++g_launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
-  record(st, 4);
+  record(st, 5);
   return DIBELLA_OK;
 }
 
@@ -2004,9 +2019,12 @@ int expand_and_queue(const uint32_t* words, const int64_t* offs, const int32_t* 
   xp.n_buckets = sch.n_buckets;
   for (int b = 0; b < DIBELLA_MAX_BUCKETS; ++b) xp.bounds[b] = sch.bucket_bounds[b];
   expand_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(xp);
+  ++g_launches;
   scan_kernel<<<1, 32, 0, st>>>(cnt, sch.n_buckets);
+  ++g_launches;
   scatter_kernel<<<grid_for(2 * n_pairs, 256), 256, 0, st>>>(
       xp.items, 2 * n_pairs, cnt, (int*)(ws + L.queue[kQNarrow]), (int*)(ws + L.queue[kQWide]));
+  ++g_launches;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "expand launch");
   return DIBELLA_OK;
@@ -2023,7 +2041,9 @@ int finish(const int32_t* lens, const dibella_pair_t* pairs, int64_t n_pairs, in
   cp.ext = ext;
   cp.results = results;
   combine_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(cp);
+  ++g_launches;
   best_of_pair_kernel<<<grid_for(n_pairs, 256), 256, 0, st>>>(pairs, n_pairs, results);
+  ++g_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "combine launch");
   return DIBELLA_OK;
@@ -2137,6 +2157,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
     else if (scoring.xdrop > 10)
       sch.narrow_max_len = min(sch.narrow_max_len, 2 * n_pairs < 7 * narrow_lanes ? 5000 : 20000);
   }
+  g_launches = 0;
   record(st, 0);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
                         scoring, results, ws, L, sch, st);
@@ -2153,12 +2174,13 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.gband = (int*)(ws + L.gband);
   ep.gcap = gcap;
   ep.forward_max = 0;
+  ep.cells_idx = 1;
   int* q[kNumQ];
   for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
   if (rc != DIBELLA_OK) return rc;
   rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
-  record(st, 5);
+  record(st, 6);
   return rc;
 }
 
@@ -2438,13 +2460,16 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
   e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const int64_t v[10] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
-                         (int64_t)c.cells[0], (int64_t)c.cells[1], (int64_t)c.cells[2],
-                         (int64_t)c.cells[3]};
-  int n = std::min(n_max, 10);
+  const int64_t v[12] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
+                         (int64_t)c.cells[0], (int64_t)(c.cells[1] + c.cells[4] + c.cells[5]),
+                         (int64_t)c.cells[2], (int64_t)c.cells[3], (int64_t)c.cells[4],
+                         (int64_t)c.cells[5]};
+  int n = std::min(n_max, 12);
   for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
 }
+
+int dibella_last_launch_count(void) { return g_launches; }
 
 const char* dibella_last_error(void) { return g_last_error.c_str(); }
 

@@ -208,9 +208,13 @@ def test_counters_report_routing(c1):
     store = dib.ReadStore.from_ascii(c1.reads, c1.offsets)
     al = dib.Aligner(store, len(c1.pairs), k=17)
     al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, **NARROW_ALL))
+    # expand, scan, scatter; narrow; wide twice; ladder 16/24/32; CTA; global; combine, best of pair
+    assert dib.dibella_last_launch_count() == 13
     c = dib.dibella_batch_counters(al.workspace)
     assert c["narrow"] == 2 * len(c1.pairs) and c["wide"] == 0
     assert c["escalated_narrow"] > 0 and c["band_overflow"] == 0
+    # the narrow escalations are finished by the wide launch on them (or above)
+    assert c["cells_wide"] == c["cells_wide_esc"] + c["cells_ladder"] and c["cells_wide_esc"] > 0
 
 
 def test_c2_full_size_sampled():
