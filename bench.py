@@ -101,7 +101,10 @@ def max_over_ranks(value: float, device=None) -> float:
 # the dominant kernel, from a one-pass ncu capture of this bench's default
 # command (profiles/ names the file and the command).  Keyed by workload, X and
 # launch; valid only for the default schedule and the kernels it was taken on.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/launch_list_c2_ecoli_bench.md: mean of the four X = 25 launches
+    ("c2_ecoli", 25, "wide form on the narrow escalations"): 608319552,
+}
 
 
 def traffic_for(workload, args, X, launch):
