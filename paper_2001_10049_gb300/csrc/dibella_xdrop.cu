@@ -603,11 +603,13 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
         my_last = 64 * (16 * q + s_hi) + 2 * lane + (int)((lm[q] >> (16 + s_hi)) & 1u);
       }
     }
+    // The three reductions are independent: issue them together so that their
+    // latencies overlap on the antidiagonal's dependency chain.
     const int last_rel = __reduce_max_sync(kFull, my_last);
-    if (last_rel < 0) break;
     const int first_rel = __reduce_min_sync(kFull, my_first);
-    const int first = 64 * cbase + first_rel, last = 64 * cbase + last_rel;
     const int vrel = __reduce_max_sync(kFull, max(pk_lo(vmax2), pk_hi(vmax2)));
+    if (last_rel < 0) break;
+    const int first = 64 * cbase + first_rel, last = 64 * cbase + last_rel;
     if (vrel + rb > best) {
       const int sl = first_rel >> 6, sh = last_rel >> 6;
       const unsigned v2 = pk_pair(vrel, vrel);
