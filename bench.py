@@ -103,7 +103,7 @@ def max_over_ranks(value: float, device=None) -> float:
 # launch; valid only for the default schedule and the kernels it was taken on.
 NCU_TRAFFIC = {
     # profiles/launch_list_c2_ecoli_bench.md: mean of the four X = 25 launches
-    ("c2_ecoli", 25, "wide form on the narrow escalations"): 608319552,
+    ("c2_ecoli", 25, "wide form on the narrow escalations"): 609061568,
 }
 
 
