@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import workloads
+from pair_flags import expected_best_of_pair
 from gpu_util import (NARROW_ALL, WIDE_ALL, assert_same, gpu_align, make_pairs, oracle_align, rc,
                       reads_to_arrays, schedule)
 
@@ -282,4 +283,25 @@ def test_full_batch_sampled(name, X, n_check):
     e2 = exp.copy()
     e2["status"] &= ~4
     assert_same(sub, e2, "%s sample X=%d" % (name, X))
+    assert ((got["status"] & 8) != 0).sum() == 0
+
+
+@pytest.mark.parametrize("name,X,n_check", [("c2_allseeds_300k", 25, 300), ("c2_ecoli_1kb", 25, 120)])
+def test_seed_options_full_batch(name, X, n_check):
+    """The seed options of Sec. 5 (every seed at least k apart; every seed at
+    least 1,000 bp apart): the whole batch launched as the benchmark runs it, a
+    seeded sample of records recomputed by the oracle, and the per-pair best
+    flags equal to the reduction of the scores over each pair's seeds."""
+    w = workloads.generate(name)
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(len(w.pairs), n_check, replace=False))
+    sc = (1, -1, -1, X)
+    got = gpu_align(w.reads, w.offsets, w.pairs, 17, sc)
+    exp = oracle_align(w.reads, w.offsets, w.pairs[idx], 17, sc)
+    sub = got[idx].copy()
+    sub["status"] &= ~4
+    e2 = exp.copy()
+    e2["status"] &= ~4
+    assert_same(sub, e2, "%s sample X=%d" % (name, X))
+    assert np.array_equal((got["status"] & 4) != 0, expected_best_of_pair(w.pairs, got))
     assert ((got["status"] & 8) != 0).sum() == 0

@@ -331,3 +331,19 @@ def test_batch_threads_and_best_of_pair():
         else:
             assert flags == []
         t = u
+
+
+def test_best_of_pair_definition_on_multi_seed_pairs():
+    """The numpy statement of the best-of-pair flag (used on whole GPU batches)
+    agrees with the oracle's flags on pairs with many seeds (the all-seed
+    option of Sec. 5)."""
+    import workloads
+    from pair_flags import expected_best_of_pair
+    w = workloads.generate("c2_allseeds_300k")
+    g = workloads.pair_groups(w.pairs)
+    many = np.flatnonzero(np.diff(g) >= 4)[:40]
+    sub = np.concatenate([w.pairs[g[i]:g[i + 1]] for i in many])
+    res = oracle.xdrop_batch(w.reads, w.offsets, sub.view(oracle.PAIR_DTYPE), 17, 1, -1, -1, 7)
+    flags = (res["status"] & oracle.STATUS_BEST_OF_PAIR) != 0
+    assert flags.sum() == len(many)
+    assert np.array_equal(flags, expected_best_of_pair(sub, res))

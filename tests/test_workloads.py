@@ -100,3 +100,26 @@ def test_stratified_sample_keeps_whole_pairs_and_longest():
     key_all = np.minimum(L[w.pairs["read_a"]], L[w.pairs["read_b"]])
     key_s = np.minimum(L[s["read_a"]], L[s["read_b"]])
     assert key_s.max() == key_all.max()
+
+
+def test_seed_options_of_sec5():
+    """One seed, all seeds at least k apart, all seeds at least 1,000 bp apart:
+    the same first seed per pair, the stated spacing, and more records as the
+    spacing shrinks."""
+    base = dict(genome_len=300_000, coverage=20.0, len_dist=1, len_a=1000.0, len_b=60000.0, seed=9)
+    one = workloads.generate(None, **base, max_seeds=1)
+    allk = workloads.generate(None, **base, max_seeds=1 << 30)
+    kb = workloads.generate(None, **base, max_seeds=1 << 30, min_seed_gap=1000)
+    k = allk.params["k"]
+    g1, gk, gb = (workloads.pair_groups(w.pairs) for w in (one, allk, kb))
+    assert len(g1) == len(gk) == len(gb)  # the same candidate pairs
+    assert np.all(np.diff(g1) == 1)
+    assert len(one.pairs) < len(kb.pairs) < len(allk.pairs)
+    for w, g, gap in ((allk, gk, k), (kb, gb, 1000)):
+        first = w.pairs[g[:-1]]
+        assert np.array_equal(first["pos_a"], one.pairs["pos_a"]) and np.array_equal(first["pos_b"], one.pairs["pos_b"])
+        pa = w.pairs["pos_a"].astype(np.int64)
+        same = np.ones(len(pa), dtype=bool)
+        same[g[:-1]] = False  # records after the first of their pair
+        assert np.all(pa[1:][same[1:]] - pa[:-1][same[1:]] >= gap)
+        assert np.all(w.pairs["seed_id"][same] == w.pairs["seed_id"][np.flatnonzero(same) - 1] + 1)

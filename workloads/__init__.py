@@ -57,7 +57,7 @@ class _Config(ctypes.Structure):
         ("err_lo", ctypes.c_double), ("err_hi", ctypes.c_double),
         ("p_sub", ctypes.c_double), ("p_ins", ctypes.c_double), ("p_del", ctypes.c_double),
         ("k", ctypes.c_int32), ("mult_lo", ctypes.c_int32), ("mult_hi", ctypes.c_int32),
-        ("max_seeds", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("max_seeds", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("min_seed_gap", ctypes.c_int32),
     ]
 
 
@@ -65,7 +65,7 @@ _BASE = dict(seed=1, genome_len=50_000, repeat_families=0, repeat_unit_len=5000,
              tandem_period_lo=2, tandem_period_hi=50, tandem_array_lo=500, tandem_array_hi=5000,
              len_dist=0, tandem_bases=0, repeat_divergence=0.03, coverage=10.0, len_a=2000.0,
              len_b=6000.0, len_mean=9000.0, len_sd=7000.0, err_lo=0.15, err_hi=0.15, p_sub=0.2,
-             p_ins=0.5, p_del=0.3, k=17, mult_lo=2, mult_hi=8, max_seeds=1)
+             p_ins=0.5, p_del=0.3, k=17, mult_lo=2, mult_hi=8, max_seeds=1, min_seed_gap=0)
 
 CONFIGS = {
     "c1_tiny": dict(_BASE),
@@ -79,12 +79,18 @@ CONFIGS = {
     "c4_repeats_small": dict(_BASE, seed=4, genome_len=5_000_000, repeat_families=10,
                              tandem_bases=50_000, coverage=40.0, len_dist=1, len_a=1000.0,
                              len_b=60000.0, mult_hi=12),
+    # The seed options of Sec. 5 on the E. coli-sized reads: every seed at least
+    # 1,000 bp apart, and (on a smaller genome) every seed at least k apart.
+    "c2_ecoli_1kb": dict(_BASE, seed=2, genome_len=4_600_000, coverage=30.0, len_dist=1,
+                         len_a=1000.0, len_b=60000.0, max_seeds=1 << 30, min_seed_gap=1000),
+    "c2_allseeds_300k": dict(_BASE, seed=5, genome_len=300_000, coverage=30.0, len_dist=1,
+                             len_a=1000.0, len_b=60000.0, max_seeds=1 << 30),
 }
 
 # Scoring of every configuration: match +1, mismatch -1, gap -1 (int32).
 SCORING = dict(match=1, mismatch=-1, gap=-1)
 XDROP = {"c1_tiny": (7,), "c2_ecoli": (7, 25), "c3_uneven": (50,), "c4_repeats": (15,),
-         "c4_repeats_small": (15,)}
+         "c4_repeats_small": (15,), "c2_ecoli_1kb": (7, 25), "c2_allseeds_300k": (7, 25)}
 
 
 def build(force: bool = False) -> str:

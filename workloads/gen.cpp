@@ -22,10 +22,11 @@
 //     distinct reads sharing a retained k-mer becomes a candidate (Sec. 8,
 //     Algorithm 1 without the multi-node owner rule); strand = XOR of the two
 //     occurrences' orientations;
-//   * seeds per pair (Sec. 8 seed constraints, Sec. 5 "separated by at least
-//     the k-mer length"): sorted by (pos_a, pos_b), the first is seed 0, each
-//     next seed is the first whose pos_a is >= k past the previous seed's,
-//     up to max_seeds.
+//   * seeds per pair (Sec. 8 seed constraints; Sec. 5 options: one seed, all
+//     seeds at least k apart, seeds at least 1,000 bp apart): sorted by
+//     (pos_a, pos_b), the first is seed 0, each next seed is the first whose
+//     pos_a is at least min_seed_gap (0 = k) past the previous seed's, up to
+//     max_seeds.
 // All random draws come from std::mt19937_64: the master stream draws read
 // lengths/starts/strands/error rates; each read's bases use their own stream
 // seeded from (seed, read index), so output does not depend on thread count.
@@ -65,7 +66,7 @@ typedef struct {
   int32_t mult_lo, mult_hi;
   int32_t max_seeds;
   int32_t n_threads;
-  int32_t pad_;
+  int32_t min_seed_gap;        // least pos_a distance between seeds of a pair (0 = k)
 } wl_config_t;
 
 typedef struct {
@@ -402,8 +403,9 @@ void make_pairs(const wl_config_t& c, Workload& w) {
       n_cand[(size_t)q] += 1;
       int taken = 0;
       int64_t last_pa = -1;
+      const int64_t gap = c.min_seed_gap > 0 ? c.min_seed_gap : k;
       for (size_t u = s; u < t && taken < c.max_seeds; ++u) {
-        if (taken > 0 && (int64_t)v[u].pa < last_pa + k) continue;
+        if (taken > 0 && (int64_t)v[u].pa < last_pa + gap) continue;
         wl_pair_t out;
         std::memset(&out, 0, sizeof(out));
         out.read_a = v[u].ra;
