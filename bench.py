@@ -57,10 +57,11 @@ def parse():
     ap.add_argument("--sample-pairs", type=int, default=0,
                     help="align a seeded sample of this many candidate pairs instead of all")
     ap.add_argument("--schedule", default=None, help="JSON dict overriding the default schedule")
-    ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve"], default="batch",
+    ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve", "candidates"], default="batch",
                     help="batch: the benchmark line (E. coli-sized, X=7 and 25); tune: uneven-length batch, "
                          "fixed vs autotuned schedule; stream: repeat-rich pairs streamed in chunks; "
-                         "serve: continuous-batching request loop at three offered loads")
+                         "serve: continuous-batching request loop at three offered loads; candidates: GPU "
+                         "candidate-pair generation (k-mer counting to seeds) on the E. coli-sized reads")
     ap.add_argument("--chunk-pairs", type=int, default=4_000_000)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -379,6 +380,103 @@ def mode_stream(args):
     }))
 
 
+# Algorithmic DRAM bytes of candidate generation: per k-mer occurrence, two
+# walks each touching one 8-byte table key and one 4-byte counter (plus the
+# 2-bit sequence, 0.5 B); per occurrence pair, the 8-byte key written once,
+# read and written by each 8-bit radix pass, read by selection and compaction.
+CAND_BYTES_PER_OCC = 24.5
+
+
+def cand_bytes_per_pair(passes: int) -> int:
+    return 8 + 16 * passes + 16
+
+
+def mode_candidates(args):
+    """Candidate pairs of the E. coli-sized read set computed on the GPU
+    (dibella_candidate_pairs: k-mer counting, multiplicity filter, pairs per
+    retained k-mer, seed selection), checked against the generator's own index,
+    timed with CUDA events from resident reads to resident seed records."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    dev = torch.device("cuda", 0)
+    w = workloads.generate(args.workload)
+    p = w.params
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    recs, st = store.candidate_pairs(k=p["k"], mult_lo=p["mult_lo"], mult_hi=p["mult_hi"], max_seeds=p["max_seeds"],
+                                     min_seed_gap=p["min_seed_gap"])
+    assert recs.tobytes() == w.pairs.view(recs.dtype).tobytes(), "GPU candidate pairs differ from the generator's"
+    ws_bytes = dib.dibella_candidate_workspace_bytes(store.n_reads, store.n_bases, p["k"], p["mult_hi"])
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = len(recs) + 1024
+    out = torch.empty((cap, 24), dtype=torch.uint8, device=dev)
+    counts = torch.zeros(6, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def call():
+        dib.dibella_candidate_pairs(store.words, store.word_offsets, store.lengths, store.n_reads, store.n_bases,
+                                    store.max_len, p["k"], p["mult_lo"], p["mult_hi"], p["max_seeds"],
+                                    p["min_seed_gap"], out, cap, counts, ws, ws_bytes, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            call()
+    torch.cuda.synchronize(dev)
+    times = []
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(7)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    c = counts.cpu().numpy()
+    assert int(c[5]) == 0 and int(c[0]) == len(recs)
+    ms = float(np.median(times))
+    pk, pk_kind = peaks()
+    rbits = max(1, int(store.n_reads - 1).bit_length())
+    pbits = max(1, int(store.max_len).bit_length())
+    passes = (2 * rbits + 2 * pbits + 1 + 7) // 8
+    alg = CAND_BYTES_PER_OCC * int(c[2]) + cand_bytes_per_pair(passes) * int(c[4])
+    n_cand = int(c[1])
+    cpu = None
+    if not args.no_cpu:
+        from oracle import candidates as oc
+        n_sub = 400
+        sub_off = w.offsets[:n_sub + 1]
+        t0 = time.perf_counter()
+        _, sst = oc.candidate_pairs(w.reads[:sub_off[-1]], sub_off, p["k"], p["mult_lo"], p["mult_hi"],
+                                    p["max_seeds"], p["min_seed_gap"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": sst["instances"] / dt, "unit": "k-mer occurrences/s", "cores": 1, "kind": "oracle",
+               "sample": "the first %d reads (%d k-mer occurrences) through the numpy oracle, %.1f s"
+                         % (n_sub, sst["instances"], dt)}
+    print(json.dumps({
+        "metric": "candidate pairs/s", "mode": "candidates", "value": n_cand / (ms * 1e-3),
+        "unit": "candidate pairs/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": w.name, "reads": int(w.n_reads), "bases": int(store.n_bases), "k": p["k"],
+                   "multiplicity": [p["mult_lo"], p["mult_hi"]], "max_seeds": p["max_seeds"],
+                   "min_seed_gap": p["min_seed_gap"], "l2": "flushed (256 MiB write) before every timed call"},
+        "kmer_occurrences_per_s": int(c[2]) / (ms * 1e-3),
+        "counts": {"seed_records": int(c[0]), "candidate_pairs": n_cand, "kmer_occurrences": int(c[2]),
+                   "retained_kmers": int(c[3]), "occurrence_pairs": int(c[4])},
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "whole call (count, allocate, fill, emit, %d radix passes, select, compact)"
+                               % passes,
+                     "peak_source": "%s hbm_gbs" % pk_kind,
+                     "bytes_model": "%.1f B per k-mer occurrence + %d B per occurrence pair"
+                                    % (CAND_BYTES_PER_OCC, cand_bytes_per_pair(passes))},
+        "matches_generator": True,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }))
+
+
 def mode_serve(args):
     """Serving loop over the E. coli-sized read store: Poisson arrivals of
     requests of 1..4096 candidate pairs (log-uniform) with X in {7, 25, 50};
@@ -440,7 +538,8 @@ def main():
         return
     if args.mode != "batch":
         if rank == 0:
-            {"tune": mode_tune, "stream": mode_stream, "serve": mode_serve}[args.mode](args)
+            {"tune": mode_tune, "stream": mode_stream, "serve": mode_serve,
+             "candidates": mode_candidates}[args.mode](args)
         return
     import torch
     import paper_2001_10049_gb300 as dib

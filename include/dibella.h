@@ -277,6 +277,49 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
                            dibella_scoring_t scoring, dibella_result_t* results,
                            void* workspace, int64_t workspace_bytes, void* stream);
 
+/* ---- candidate pairs --------------------------------------------------- */
+
+/* The steps before alignment, on the GPU: every k-mer occurrence of every read
+ * in canonical orientation (Sec. 3: the smaller 2-bit code, A<C<G<T, of the
+ * k-mer and of its reverse complement; orientation 1 when the reverse
+ * complement is the smaller), its multiplicity over all occurrences, the
+ * k-mers retained for mult_lo <= multiplicity <= mult_hi (Sec. 3-4), every
+ * pair of distinct reads sharing a retained k-mer once per pair of
+ * occurrences (Sec. 8, Algorithm 1; read_a < read_b, positions in forward
+ * coordinates, strand = XOR of the orientations), and per read pair the seeds
+ * (Sec. 8 seed constraints, Sec. 5 options): occurrences sorted by (pos_a,
+ * pos_b, strand), seed 0 the first, each next seed the first whose pos_a is
+ * at least min_seed_gap (0 = k) past the previous seed's, up to max_seeds.
+ *
+ * Workspace bytes for reads of n_bases bases in total (a hash table of 1.5 to
+ * 3 slots per base, the retained occurrences and room for n_bases x
+ * (mult_hi - 1) / 2 occurrence pairs: about 50 to 92 + 12 x (mult_hi - 1)
+ * bytes per base).  EINVAL outside 1 <= k <= 32,
+ * 1 <= mult_hi <= 32. */
+int dibella_candidate_workspace_bytes(int64_t n_reads, int64_t n_bases, int32_t k, int32_t mult_hi,
+                                      int64_t* bytes_out);
+
+/* DEVICE pointers: the store (packed_words, read_word_offsets, read_lengths
+ * of n_reads reads, n_bases bases in total, none longer than max_read_len),
+ * pairs_out (pairs_capacity records), counts_out (6 int64), workspace
+ * (256-byte aligned, workspace_bytes >= the size above).  Asynchronous on
+ * `stream` (a cudaStream_t); nothing is allocated.  Writes the seed records
+ * sorted by (read_a, read_b, seed_id) and counts_out = {seed records,
+ * candidate pairs, k-mer occurrences, retained k-mers, occurrence pairs,
+ * status}; status 0 = complete, else bit 0 the hash table filled, bit 1 more
+ * occurrence pairs than the workspace holds, bit 2 more seed records than
+ * pairs_capacity, bit 3 more occurrences than n_bases (the records are then
+ * incomplete).  Synchronous EINVAL: k outside 1..32, 1 <= mult_lo <= mult_hi
+ * <= 32 violated, max_seeds < 1, min_seed_gap < 0, max_read_len outside
+ * 0..DIBELLA_MAX_READ_LEN, null or misaligned buffers, or read and position
+ * fields that do not pack into one 64-bit sort key (2 x bits(n_reads - 1) +
+ * 2 x bits(max_read_len) + 1 > 64); ENOMEM when the workspace is too small. */
+int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                            const int32_t* read_lengths, int64_t n_reads, int64_t n_bases, int32_t max_read_len,
+                            int32_t k, int32_t mult_lo, int32_t mult_hi, int32_t max_seeds, int32_t min_seed_gap,
+                            dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
+                            void* workspace, int64_t workspace_bytes, void* stream);
+
 /* ---- autotuning -------------------------------------------------------- */
 /* Pick a schedule for batches like this one: runs dibella_xdrop_batch on the
  * given (sample) batch with candidate schedules and returns the fastest in

@@ -115,6 +115,9 @@ def _lib():
             "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
             "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
             "dibella_last_launch_count": ([], i32),
+            "dibella_candidate_workspace_bytes": ([i64, i64, i32, i32, p64], i32),
+            "dibella_candidate_pairs": ([vp, vp, vp, i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64,
+                                         vp], i32),
             "dibella_last_error": ([], ctypes.c_char_p),
             "dibella_version": ([], ctypes.c_char_p),
         }
@@ -203,6 +206,22 @@ def dibella_xdrop_workspace_bytes(n_pairs: int, max_read_len: int) -> int:
     _check(_lib().dibella_xdrop_workspace_bytes(n_pairs, max_read_len, ctypes.byref(out)),
            "dibella_xdrop_workspace_bytes")
     return out.value
+
+
+def dibella_candidate_workspace_bytes(n_reads: int, n_bases: int, k: int, mult_hi: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_candidate_workspace_bytes(n_reads, n_bases, k, mult_hi, ctypes.byref(out)),
+           "dibella_candidate_workspace_bytes")
+    return out.value
+
+
+def dibella_candidate_pairs(words, word_offsets, lengths, n_reads: int, n_bases: int, max_read_len: int, k: int,
+                            mult_lo: int, mult_hi: int, max_seeds: int, min_seed_gap: int, pairs_out,
+                            pairs_capacity: int, counts_out, workspace, workspace_bytes: int, stream=None) -> None:
+    _check(_lib().dibella_candidate_pairs(_ptr(words), _ptr(word_offsets), _ptr(lengths), n_reads, n_bases,
+                                          max_read_len, k, mult_lo, mult_hi, max_seeds, min_seed_gap,
+                                          _ptr(pairs_out), pairs_capacity, _ptr(counts_out), _ptr(workspace),
+                                          workspace_bytes, _stream_handle(stream)), "dibella_candidate_pairs")
 
 
 def dibella_staging_bytes(n_pairs: int) -> int:

@@ -1,0 +1,616 @@
+// Candidate pairs on the GPU: the steps diBELLA runs before alignment.
+//
+//   Sec. 3      every k-mer occurrence of every read, in canonical orientation
+//               (the smaller 2-bit code of the k-mer and of its reverse
+//               complement), counted over all occurrences;
+//   Sec. 3-4    a k-mer is retained when its multiplicity is in [mult_lo, mult_hi];
+//   Sec. 8      (overlap detection, Algorithm 1) every pair of distinct reads that
+//               share a retained k-mer, once per pair of occurrences, with both
+//               positions and the strand (1 when the orientations differ);
+//   Sec. 8, 5   seed constraints: per read pair, occurrences sorted by (pos_a,
+//               pos_b, strand); seed 0 is the first, each next seed the first
+//               whose pos_a is at least min_seed_gap (0 = k) past the last one,
+//               up to max_seeds.
+//
+// GPU design (one pass over the read store per hash step, everything else
+// linear in the retained occurrences):
+//   count    a warp per read, a lane per position: the canonical code from the
+//            2-bit store, inserted into an open-addressing table (64-bit keys,
+//            linear probing, bounded probes) whose slot counts the occurrences;
+//   allocate a thread per slot: retained slots get a segment of the occurrence
+//            array (atomic cursor) and join the retained list;
+//   fill     the same walk as count: each retained occurrence is written into
+//            its k-mer's segment as (read << 32 | pos << 1 | orientation);
+//   emit     a thread per retained k-mer sorts its (at most mult_hi)
+//            occurrences and appends one 64-bit key per occurrence pair:
+//            read_a | read_b | pos_a | pos_b | strand, packed most significant
+//            first with bit widths from the read count and the longest read;
+//   sort     LSD radix sort of those keys (8-bit digits, stable: per-tile
+//            digit histograms, one scan, warp-match ranking in the scatter);
+//   select   a thread per run start (a new (read_a, read_b)) applies the
+//            greedy seed rule along its run;
+//   compact  a scan of the selection flags writes the 24-byte pair records,
+//            sorted by (read_a, read_b, seed_id).
+// Nothing here waits on another block; every probe loop is bounded.
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/dibella.h"
+
+namespace {
+
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+constexpr unsigned long long kEmptyKey = ~0ull;  // no canonical code equals it (see insert)
+constexpr unsigned long long kNoBase = ~0ull;
+constexpr int kMaxProbe = 1 << 14;
+constexpr int kMaxMult = 32;
+constexpr int kScanThreads = 1024;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kTile = kSortThreads * kSortItems;  // keys per sort / scan tile
+
+// Device counters of one call (also copied to the caller's counts array).
+struct CandState {
+  unsigned long long instances;   // k-mer occurrences
+  unsigned long long retained;    // retained k-mers
+  unsigned long long inst_cursor; // retained occurrences placed
+  unsigned long long occ_pairs;   // occurrence pairs emitted
+  unsigned long long n_keys;      // occurrence-pair keys held (occ_pairs, capped at the capacity)
+  unsigned long long candidates;  // distinct (read_a, read_b)
+  unsigned long long seeds;       // seed records written
+  unsigned int status;            // bit 0 table full, bit 1 pair capacity, bit 2 output
+                                  // capacity, bit 3 occurrence capacity
+  unsigned int pad;
+};
+
+// Warp-aggregated atomicAdd: every lane of the warp calls it (v = 0 allowed);
+// each lane gets the old value plus the sum of v over the lanes below it.
+__device__ __forceinline__ unsigned long long warp_atomic_add(unsigned long long* addr, unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned long long total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(addr, total);
+  base = __shfl_sync(0xFFFFFFFFu, base, 31);
+  return base + incl - v;
+}
+
+struct KeyLayout {  // bit positions of the packed occurrence-pair key
+  int sh_ra, sh_rb, sh_pa, sh_pb;
+  unsigned long long m_read, m_pos;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+// k bases of the forward copy starting at base index idx, base t at bits 2t.
+__device__ __forceinline__ unsigned long long bases_le(const uint32_t* __restrict__ words, long long idx,
+                                                       int k) {
+  const long long w = idx >> 4;
+  const int sh = (int)(idx & 15) * 2;
+  const unsigned long long lo = (unsigned long long)__ldg(words + w) | ((unsigned long long)__ldg(words + w + 1) << 32);
+  unsigned long long x = lo >> sh;
+  if (sh > 0 && sh + 2 * k > 64) x |= (unsigned long long)__ldg(words + w + 2) << (64 - sh);
+  return k == 32 ? x : (x & ((1ull << (2 * k)) - 1ull));
+}
+
+// Canonical code and orientation of the k-mer whose bases (first at bits 0-1)
+// are x: the forward code has the first base most significant; the reverse
+// complement code is the complement of x (its first base is the complement of
+// the k-mer's last).  A code of all ones would need fw = rc = 2^64-1, i.e.
+// x = 0 and fw = 0: so no canonical code equals kEmptyKey.
+__device__ __forceinline__ unsigned long long canonical(unsigned long long x, int k, unsigned* orient) {
+  unsigned long long y = __brevll(x);
+  y = ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
+  const unsigned long long fw = k == 32 ? y : (y >> (64 - 2 * k));
+  const unsigned long long rc = k == 32 ? ~x : (x ^ ((1ull << (2 * k)) - 1ull));
+  *orient = fw > rc ? 1u : 0u;
+  return fw <= rc ? fw : rc;
+}
+
+struct TableRef {
+  unsigned long long* keys;
+  unsigned int* counts;
+  unsigned long long* base;
+  unsigned int* fill;
+  unsigned long long mask;  // slots - 1
+};
+
+__device__ long long table_insert(const TableRef& t, unsigned long long key, CandState* st) {
+  unsigned long long s = mix64(key) & t.mask;
+  for (int i = 0; i < kMaxProbe; ++i) {
+    const unsigned long long cur = t.keys[s];
+    if (cur == key) return (long long)s;
+    if (cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS(t.keys + s, kEmptyKey, key);
+      if (prev == kEmptyKey || prev == key) return (long long)s;
+    }
+    s = (s + 1) & t.mask;
+  }
+  atomicOr(&st->status, 1u);
+  return -1;
+}
+
+__device__ long long table_find(const TableRef& t, unsigned long long key) {
+  unsigned long long s = mix64(key) & t.mask;
+  for (int i = 0; i < kMaxProbe; ++i) {
+    const unsigned long long cur = t.keys[s];
+    if (cur == key) return (long long)s;
+    if (cur == kEmptyKey) return -1;
+    s = (s + 1) & t.mask;
+  }
+  return -1;
+}
+
+struct StoreRef {
+  const uint32_t* words;
+  const int64_t* word_offsets;
+  const int32_t* lengths;
+  long long n_reads;
+  int k;
+};
+
+// Pass 1 (count) and pass 3 (fill) share the walk over every k-mer occurrence.
+template <bool kFill>
+__global__ void kmer_walk_kernel(StoreRef sr, TableRef t, unsigned long long* inst, unsigned long long inst_cap,
+                                 CandState* st) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = warp; r < sr.n_reads; r += n_warps) {
+    const long long len = sr.lengths[r];
+    const long long first = sr.word_offsets[r] * 16;
+    for (long long p = lane; p + sr.k <= len; p += 32) {
+      unsigned orient;
+      const unsigned long long c = canonical(bases_le(sr.words, first + p, sr.k), sr.k, &orient);
+      if (!kFill) {
+        const long long s = table_insert(t, c, st);
+        if (s >= 0) atomicAdd(t.counts + s, 1u);
+      } else {
+        const long long s = table_find(t, c);
+        if (s < 0) continue;
+        const unsigned long long b = t.base[s];
+        if (b == kNoBase) continue;
+        const unsigned slot = atomicAdd(t.fill + s, 1u);
+        if (b + slot >= inst_cap) {
+          atomicOr(&st->status, 8u);
+          continue;
+        }
+        inst[b + slot] = ((unsigned long long)r << 32) | ((unsigned long long)p << 1) | orient;
+      }
+    }
+  }
+}
+
+// Pass 2: retained slots get their occurrence segment (warp-aggregated atomics;
+// every lane runs the same iterations).
+__global__ void allocate_kernel(TableRef t, unsigned long long n_slots, int mult_lo, int mult_hi,
+                                unsigned int* retained_list, CandState* st) {
+  const unsigned long long lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n_slots;
+       w0 += stride) {
+    const unsigned long long s = w0 + lane;
+    const bool occ = s < n_slots && t.keys[s] != kEmptyKey;
+    const unsigned c = occ ? t.counts[s] : 0u;
+    const bool keep = occ && (int)c >= mult_lo && (int)c <= mult_hi;
+    warp_atomic_add(&st->instances, c);
+    const unsigned long long b = warp_atomic_add(&st->inst_cursor, keep ? c : 0u);
+    const unsigned long long r = warp_atomic_add(&st->retained, keep ? 1u : 0u);
+    if (occ) t.base[s] = keep ? b : kNoBase;
+    if (keep) retained_list[r] = (unsigned int)s;
+  }
+}
+
+// Pass 4: occurrence pairs of every retained k-mer, as packed keys.
+__global__ void emit_pairs_kernel(TableRef t, const unsigned int* retained_list, const unsigned long long* inst,
+                                  unsigned long long inst_cap, KeyLayout kl, unsigned long long* keys_out,
+                                  unsigned long long capacity, CandState* st) {
+  const unsigned long long n = st->retained;
+  const unsigned long long lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n;
+       w0 += stride) {
+    const unsigned long long i = w0 + lane;
+    unsigned long long v[kMaxMult];
+    int c = 0, n_pairs = 0;
+    if (i < n) {
+      const unsigned s = retained_list[i];
+      c = (int)t.counts[s];
+      const unsigned long long b = t.base[s];
+      if (b + c > inst_cap) c = 0;  // its occurrences did not fit (status bit 3 is set)
+      for (int x = 0; x < c; ++x) v[x] = inst[b + x];
+      for (int x = 1; x < c; ++x) {  // insertion sort by (read, pos, orientation)
+        const unsigned long long e = v[x];
+        int y = x - 1;
+        while (y >= 0 && v[y] > e) {
+          v[y + 1] = v[y];
+          --y;
+        }
+        v[y + 1] = e;
+      }
+      for (int x = 0; x < c; ++x)
+        for (int y = x + 1; y < c; ++y) n_pairs += (v[x] >> 32) != (v[y] >> 32);
+    }
+    const unsigned long long at = warp_atomic_add(&st->occ_pairs, (unsigned long long)n_pairs);
+    if (n_pairs == 0) continue;
+    if (at + n_pairs > capacity) {
+      atomicOr(&st->status, 2u);
+      continue;
+    }
+    unsigned long long o = at;
+    for (int x = 0; x < c; ++x)
+      for (int y = x + 1; y < c; ++y) {
+        const unsigned long long ra = v[x] >> 32, rb = v[y] >> 32;
+        if (ra == rb) continue;
+        const unsigned long long pa = (v[x] >> 1) & 0x7FFFFFFFull, pb = (v[y] >> 1) & 0x7FFFFFFFull;
+        const unsigned long long strand = (v[x] ^ v[y]) & 1ull;
+        keys_out[o++] = (ra << kl.sh_ra) | (rb << kl.sh_rb) | (pa << kl.sh_pa) | (pb << kl.sh_pb) | strand;
+      }
+  }
+}
+
+// The keys held: the pairs emitted, capped at the capacity (a capped run is
+// flagged in status bit 1 and its results are incomplete).
+__global__ void cap_keys_kernel(CandState* st, unsigned long long capacity) {
+  st->n_keys = st->occ_pairs < capacity ? st->occ_pairs : capacity;
+}
+
+// ---- LSD radix sort of 64-bit keys (8-bit digits) ------------------------
+
+__global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, const CandState* st, int shift,
+                                  unsigned int* hist, unsigned long long n_tiles_max) {
+  __shared__ unsigned int h[256];
+  const unsigned long long n = st->n_keys;
+  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  for (unsigned long long tile = blockIdx.x; tile < n_tiles && tile < n_tiles_max; tile += gridDim.x) {
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long t0 = tile * kTile;
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * kSortThreads + threadIdx.x;
+      if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(unsigned long long)threadIdx.x * n_tiles + tile] = h[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Exclusive scan, in place, of len u32 counts into u64 offsets (one block).
+__global__ void scan_counts_kernel(const unsigned int* counts, unsigned long long* offsets, const CandState* st,
+                                   int per_digit, unsigned long long fixed_len) {
+  __shared__ unsigned long long part[kScanThreads];
+  unsigned long long len = fixed_len;
+  if (per_digit == 1) len = 256ull * ((st->n_keys + kTile - 1) / kTile);
+  if (per_digit == 2) len = (st->n_keys + kTile - 1) / kTile;
+  const unsigned long long chunk = (len + kScanThreads - 1) / kScanThreads;
+  const unsigned long long lo = threadIdx.x * chunk;
+  unsigned long long sum = 0;
+  for (unsigned long long i = lo; i < lo + chunk && i < len; ++i) sum += counts[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int i = 0; i < kScanThreads; ++i) {
+      const unsigned long long v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  unsigned long long acc = part[threadIdx.x];
+  for (unsigned long long i = lo; i < lo + chunk && i < len; ++i) {
+    const unsigned long long v = counts[i];
+    offsets[i] = acc;
+    acc += v;
+  }
+}
+
+__global__ void digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
+                                     const CandState* st, int shift, const unsigned long long* offsets) {
+  __shared__ unsigned long long base[256];
+  __shared__ unsigned int wcnt[kSortThreads / 32][257];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned long long n = st->n_keys;
+  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    base[threadIdx.x] = offsets[(unsigned long long)threadIdx.x * n_tiles + tile];
+    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long t0 = tile * kTile;
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned long long i = t0 + (unsigned long long)j * kSortThreads + threadIdx.x;
+      const bool ok = i < n;
+      const unsigned long long key = ok ? in[i] : 0ull;
+      const unsigned d = ok ? (unsigned)((key >> shift) & 255u) : 256u;
+      const unsigned peers = __match_any_sync(kFullMask, d);
+      const unsigned rank = __popc(peers & lt);
+      if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+      __syncthreads();
+      if (ok) {
+        unsigned long long pos = base[d] + rank;
+        for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+        out[pos] = key;
+      }
+      __syncthreads();
+      unsigned tot = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        tot += wcnt[w][threadIdx.x];
+        wcnt[w][threadIdx.x] = 0;
+      }
+      base[threadIdx.x] += tot;
+      __syncthreads();
+    }
+  }
+}
+
+// ---- seed selection and compaction -----------------------------------------
+
+// A thread per run start walks its run: selection flags and seed ids.
+__global__ void select_kernel(const unsigned long long* __restrict__ keys, CandState* st, KeyLayout kl,
+                              int max_seeds, int gap, unsigned int* flags, unsigned int* sid) {
+  const unsigned long long n = st->n_keys;
+  const unsigned long long lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n;
+       w0 += stride) {
+    const unsigned long long i = w0 + lane;
+    const bool start = i < n && (i == 0 || (keys[i - 1] >> kl.sh_rb) != (keys[i] >> kl.sh_rb));
+    warp_atomic_add(&st->candidates, start ? 1u : 0u);
+    if (!start) continue;
+    const unsigned long long run = keys[i] >> kl.sh_rb;
+    int taken = 0;
+    long long last = 0;
+    for (unsigned long long u = i; u < n && (keys[u] >> kl.sh_rb) == run; ++u) {
+      const long long pa = (long long)((keys[u] >> kl.sh_pa) & kl.m_pos);
+      const bool take = taken < max_seeds && (taken == 0 || pa >= last + gap);
+      flags[u] = take ? 1u : 0u;
+      sid[u] = take ? (unsigned)taken : 0u;
+      if (take) {
+        last = pa;
+        ++taken;
+      }
+    }
+  }
+}
+
+// Per-tile sums of the flags.
+__global__ void tile_sum_kernel(const unsigned int* flags, const CandState* st, unsigned int* sums) {
+  __shared__ unsigned int s[kSortThreads];
+  const unsigned long long n = st->n_keys;
+  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    unsigned int v = 0;
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned long long i = tile * kTile + (unsigned long long)threadIdx.x * kSortItems + j;
+      if (i < n) v += flags[i];
+    }
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kSortThreads / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[tile] = s[0];
+    __syncthreads();
+  }
+}
+
+__global__ void compact_kernel(const unsigned long long* __restrict__ keys, const unsigned int* flags,
+                               const unsigned int* sid, const unsigned long long* tile_off, CandState* st,
+                               KeyLayout kl, dibella_pair_t* out, unsigned long long capacity) {
+  __shared__ unsigned int s[kSortThreads];
+  const unsigned long long n = st->n_keys;
+  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const unsigned long long i0 = tile * kTile + (unsigned long long)threadIdx.x * kSortItems;
+    unsigned int v = 0;
+    for (int j = 0; j < kSortItems; ++j)
+      if (i0 + j < n) v += flags[i0 + j];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive scan of the 256 thread sums
+      unsigned int acc = 0;
+      for (int t = 0; t < kSortThreads; ++t) {
+        const unsigned int x = s[t];
+        s[t] = acc;
+        acc += x;
+      }
+    }
+    __syncthreads();
+    unsigned long long o = tile_off[tile] + s[threadIdx.x];
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned long long i = i0 + j;
+      if (i >= n || !flags[i]) continue;
+      if (o >= capacity) {
+        atomicOr(&st->status, 4u);
+        ++o;
+        continue;
+      }
+      const unsigned long long key = keys[i];
+      dibella_pair_t r;
+      r.read_a = (uint32_t)((key >> kl.sh_ra) & kl.m_read);
+      r.read_b = (uint32_t)((key >> kl.sh_rb) & kl.m_read);
+      r.pos_a = (uint32_t)((key >> kl.sh_pa) & kl.m_pos);
+      r.pos_b = (uint32_t)((key >> kl.sh_pb) & kl.m_pos);
+      r.strand = (uint8_t)(key & 1ull);
+      r.pad[0] = r.pad[1] = r.pad[2] = 0;
+      r.seed_id = sid[i];
+      out[o++] = r;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void finish_kernel(CandState* st, const unsigned long long* tile_off, const unsigned int* tile_sums,
+                              int64_t* counts_out) {
+  const unsigned long long n = st->n_keys;
+  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  st->seeds = n_tiles ? tile_off[n_tiles - 1] + tile_sums[n_tiles - 1] : 0;
+  counts_out[0] = (int64_t)st->seeds;
+  counts_out[1] = (int64_t)st->candidates;
+  counts_out[2] = (int64_t)st->instances;
+  counts_out[3] = (int64_t)st->retained;
+  counts_out[4] = (int64_t)st->occ_pairs;
+  counts_out[5] = (int64_t)st->status;
+}
+
+int bits_for(unsigned long long v) {  // bits needed for values 0..v
+  int b = 1;
+  while (b < 63 && (v >> b) != 0) ++b;
+  return b;
+}
+
+struct CandLayout {
+  unsigned long long slots;  // hash table slots (power of two)
+  unsigned long long inst;   // occurrence capacity
+  unsigned long long pairs;  // occurrence-pair capacity
+  unsigned long long tiles;  // sort tiles
+  size_t state, keys, counts, base, fill, retained, inst_arr, pk0, pk1, hist, hoff, flags, sid, tsum, toff, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+CandLayout cand_layout(long long n_bases, int k, int mult_hi) {
+  CandLayout L;
+  const unsigned long long inst = (unsigned long long)(n_bases > 0 ? n_bases : 1);
+  unsigned long long slots = 1024;
+  while (slots < inst + inst / 2) slots <<= 1;  // load factor below 2/3
+  L.slots = slots;
+  L.inst = inst;
+  L.pairs = inst * (unsigned long long)(mult_hi > 1 ? mult_hi - 1 : 1) / 2 + 1;
+  L.tiles = (L.pairs + kTile - 1) / kTile;
+  (void)k;
+  size_t off = 0;
+  L.state = off;    off = align256(off + sizeof(CandState));
+  L.keys = off;     off = align256(off + 8 * slots);
+  L.counts = off;   off = align256(off + 4 * slots);
+  L.base = off;     off = align256(off + 8 * slots);
+  L.fill = off;     off = align256(off + 4 * slots);
+  L.retained = off; off = align256(off + 4 * slots);
+  L.inst_arr = off; off = align256(off + 8 * inst);
+  L.pk0 = off;      off = align256(off + 8 * L.pairs);
+  L.pk1 = off;      off = align256(off + 8 * L.pairs);
+  L.hist = off;     off = align256(off + 4 * 256 * L.tiles);
+  L.hoff = off;     off = align256(off + 8 * 256 * L.tiles);
+  L.flags = off;    off = align256(off + 4 * L.pairs);
+  L.sid = off;      off = align256(off + 4 * L.pairs);
+  L.tsum = off;     off = align256(off + 4 * L.tiles);
+  L.toff = off;     off = align256(off + 8 * L.tiles);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dibella_candidate_workspace_bytes(int64_t n_reads, int64_t n_bases, int32_t k, int32_t mult_hi,
+                                      int64_t* bytes_out) {
+  if (!bytes_out || n_reads < 0 || n_bases < 0 || k < 1 || k > 32 || mult_hi < 1 || mult_hi > kMaxMult)
+    return DIBELLA_EINVAL;
+  *bytes_out = (int64_t)cand_layout(n_bases, k, mult_hi).total;
+  return DIBELLA_OK;
+}
+
+int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                            const int32_t* read_lengths, int64_t n_reads, int64_t n_bases, int32_t max_read_len,
+                            int32_t k, int32_t mult_lo, int32_t mult_hi, int32_t max_seeds, int32_t min_seed_gap,
+                            dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
+                            void* workspace, int64_t workspace_bytes, void* stream) {
+  if (n_reads < 0 || n_bases < 0 || k < 1 || k > 32 || mult_lo < 1 || mult_hi < mult_lo || mult_hi > kMaxMult ||
+      max_seeds < 1 || min_seed_gap < 0 || max_read_len < 0 || max_read_len > DIBELLA_MAX_READ_LEN ||
+      pairs_capacity < 0 || !counts_out || !workspace || ((uintptr_t)workspace & 255))
+    return DIBELLA_EINVAL;
+  if (n_reads > 0 && (!packed_words || !read_word_offsets || !read_lengths)) return DIBELLA_EINVAL;
+  if (pairs_capacity > 0 && !pairs_out) return DIBELLA_EINVAL;
+  const int rbits = bits_for(n_reads > 0 ? (unsigned long long)(n_reads - 1) : 0);
+  const int pbits = bits_for(max_read_len > 0 ? (unsigned long long)max_read_len : 0);
+  if (2 * rbits + 2 * pbits + 1 > 64) return DIBELLA_EINVAL;
+  const CandLayout L = cand_layout(n_bases, k, mult_hi);
+  if ((unsigned long long)workspace_bytes < L.total) return DIBELLA_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  CandState* state = (CandState*)(ws + L.state);
+  TableRef t;
+  t.keys = (unsigned long long*)(ws + L.keys);
+  t.counts = (unsigned int*)(ws + L.counts);
+  t.base = (unsigned long long*)(ws + L.base);
+  t.fill = (unsigned int*)(ws + L.fill);
+  t.mask = L.slots - 1;
+  unsigned int* retained = (unsigned int*)(ws + L.retained);
+  unsigned long long* inst = (unsigned long long*)(ws + L.inst_arr);
+  unsigned long long* pk0 = (unsigned long long*)(ws + L.pk0);
+  unsigned long long* pk1 = (unsigned long long*)(ws + L.pk1);
+  unsigned int* hist = (unsigned int*)(ws + L.hist);
+  unsigned long long* hoff = (unsigned long long*)(ws + L.hoff);
+  unsigned int* flags = (unsigned int*)(ws + L.flags);
+  unsigned int* sid = (unsigned int*)(ws + L.sid);
+  unsigned int* tsum = (unsigned int*)(ws + L.tsum);
+  unsigned long long* toff = (unsigned long long*)(ws + L.toff);
+
+  KeyLayout kl;
+  kl.sh_pb = 1;
+  kl.sh_pa = 1 + pbits;
+  kl.sh_rb = 1 + 2 * pbits;
+  kl.sh_ra = 1 + 2 * pbits + rbits;
+  kl.m_read = (1ull << rbits) - 1ull;
+  kl.m_pos = (1ull << pbits) - 1ull;
+
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
+  if ((e = cudaMemsetAsync(t.keys, 0xFF, 8 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
+  if ((e = cudaMemsetAsync(t.counts, 0, 4 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
+  if ((e = cudaMemsetAsync(t.fill, 0, 4 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  StoreRef sr{packed_words, read_word_offsets, read_lengths, (long long)n_reads, k};
+  const int walk_blocks = sms * 16;
+  if (n_reads > 0) {
+    kmer_walk_kernel<false><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, state);
+    allocate_kernel<<<sms * 8, 256, 0, st>>>(t, L.slots, mult_lo, mult_hi, retained, state);
+    kmer_walk_kernel<true><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, state);
+    emit_pairs_kernel<<<sms * 8, 256, 0, st>>>(t, retained, inst, L.inst, kl, pk0, L.pairs, state);
+  }
+  cap_keys_kernel<<<1, 1, 0, st>>>(state, L.pairs);
+  // Radix sort by the whole key (read_a, read_b, pos_a, pos_b, strand).
+  const int key_bits = kl.sh_ra + rbits;
+  const int passes = (key_bits + 7) / 8;
+  unsigned long long* src = pk0;
+  unsigned long long* dst = pk1;
+  const int sort_blocks = sms * 8;
+  for (int pss = 0; pss < passes; ++pss) {
+    digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, state, 8 * pss, hist, L.tiles);
+    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, state, 1, 0);
+    digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, dst, state, 8 * pss, hoff);
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  select_kernel<<<sms * 8, 256, 0, st>>>(src, state, kl, max_seeds, min_seed_gap > 0 ? min_seed_gap : k, flags, sid);
+  tile_sum_kernel<<<sort_blocks, kSortThreads, 0, st>>>(flags, state, tsum);
+  scan_counts_kernel<<<1, kScanThreads, 0, st>>>(tsum, toff, state, 2, 0);
+  compact_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, flags, sid, toff, state, kl, pairs_out,
+                                                         (unsigned long long)pairs_capacity);
+  finish_kernel<<<1, 1, 0, st>>>(state, toff, tsum, counts_out);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DIBELLA_OK : DIBELLA_ECUDA;
+}
+
+}  // extern "C"

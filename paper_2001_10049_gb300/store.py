@@ -37,6 +37,37 @@ class ReadStore:
     def nbytes(self) -> int:
         return self.words.numel() * 4 + self.word_offsets.numel() * 8 + self.lengths.numel() * 4
 
+    def candidate_pairs(self, k: int = 17, mult_lo: int = 2, mult_hi: int = 8, max_seeds: int = 1,
+                        min_seed_gap: int = 0, stream=None, workspace=None):
+        """Seed records of every candidate pair of the store's reads, computed on
+        the GPU by dibella_candidate_pairs (k-mer counting, multiplicity filter,
+        pairs per retained k-mer, seed selection), and its counts.  Synchronous:
+        returns (records as a numpy PAIR_DTYPE array, dict of counts)."""
+        from . import PAIR_DTYPE, dibella_candidate_pairs, dibella_candidate_workspace_bytes
+        torch = _torch()
+        dev = self.words.device
+        ws_bytes = dibella_candidate_workspace_bytes(self.n_reads, self.n_bases, k, mult_hi)
+        if workspace is None or workspace.numel() < ws_bytes:
+            workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        counts = torch.zeros(6, dtype=torch.int64, device=dev)
+        cap = max(1024, self.n_bases // 16)
+        for _ in range(2):
+            out = torch.empty((cap, 24), dtype=torch.uint8, device=dev)
+            dibella_candidate_pairs(self.words, self.word_offsets, self.lengths, self.n_reads, self.n_bases,
+                                    self.max_len, k, mult_lo, mult_hi, max_seeds, min_seed_gap, out, cap, counts,
+                                    workspace, ws_bytes, stream)
+            torch.cuda.synchronize(dev)
+            c = counts.cpu().numpy()
+            if not (int(c[5]) & 4):
+                break
+            cap = int(c[0])  # the seed records did not fit: once more, exactly sized
+        stats = dict(zip(["seeds", "candidate_pairs", "instances", "retained_kmers", "occurrence_pairs", "status"],
+                         (int(v) for v in c)))
+        if stats["status"]:
+            raise RuntimeError("dibella_candidate_pairs incomplete, status %d" % stats["status"])
+        recs = out[:stats["seeds"]].cpu().numpy().reshape(-1).view(PAIR_DTYPE)
+        return recs, stats
+
 
 class Aligner:
     """Runs dibella_xdrop_batch on a ReadStore with a reusable workspace."""
