@@ -15,12 +15,15 @@
 // GPU design (one pass over the read store per hash step, everything else
 // linear in the retained occurrences):
 //   count    a warp per read, a lane per position: the canonical code from the
-//            2-bit store, inserted into an open-addressing table (64-bit keys,
-//            linear probing, bounded probes) whose slot counts the occurrences;
-//   allocate a thread per slot: retained slots get a segment of the occurrence
-//            array (atomic cursor) and join the retained list;
-//   fill     the same walk as count: each retained occurrence is written into
-//            its k-mer's segment as (read << 32 | pos << 1 | orientation);
+//            2-bit store, inserted into an open-addressing table (16-byte slots
+//            of key + 1, count and cursor, so that one probe touches one
+//            sector; linear probing, bounded probes) that counts occurrences;
+//   allocate each lane takes 16 slots: retained slots get a segment of the
+//            occurrence array (one warp-aggregated atomic per 512 slots) and
+//            join the retained list;
+//   fill     the same walk as count: each retained occurrence takes the next
+//            place of its k-mer's segment (an atomic on the slot's cursor) as
+//            (read << 32 | pos << 1 | orientation);
 //   emit     a thread per retained k-mer sorts its (at most mult_hi)
 //            occurrences and appends one 64-bit key per occurrence pair:
 //            read_a | read_b | pos_a | pos_b | strand, packed most significant
@@ -42,13 +45,13 @@
 namespace {
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
-constexpr unsigned long long kEmptyKey = ~0ull;  // no canonical code equals it (see insert)
-constexpr unsigned long long kNoBase = ~0ull;
+constexpr unsigned long long kEmptyKey = 0ull;  // slots hold canonical code + 1 (see canonical)
 constexpr int kMaxProbe = 1 << 14;
 constexpr int kMaxMult = 32;
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 64;
+constexpr int kAllocPerLane = 16;
 constexpr int kTile = kSortThreads * kSortItems;  // keys per sort / scan tile
 
 // Device counters of one call (also copied to the caller's counts array).
@@ -110,7 +113,7 @@ __device__ __forceinline__ unsigned long long bases_le(const uint32_t* __restric
 // are x: the forward code has the first base most significant; the reverse
 // complement code is the complement of x (its first base is the complement of
 // the k-mer's last).  A code of all ones would need fw = rc = 2^64-1, i.e.
-// x = 0 and fw = 0: so no canonical code equals kEmptyKey.
+// x = 0 and fw = 0: so code + 1 never wraps to the empty key 0.
 __device__ __forceinline__ unsigned long long canonical(unsigned long long x, int k, unsigned* orient) {
   unsigned long long y = __brevll(x);
   y = ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
@@ -120,21 +123,26 @@ __device__ __forceinline__ unsigned long long canonical(unsigned long long x, in
   return fw <= rc ? fw : rc;
 }
 
+// One table slot: canonical code + 1 (0 = empty), occurrence count, and the
+// cursor into the k-mer's occurrence segment (set by allocate, advanced by fill).
+struct __align__(16) Slot {
+  unsigned long long key;
+  unsigned int count;
+  unsigned int cursor;
+};
+
 struct TableRef {
-  unsigned long long* keys;
-  unsigned int* counts;
-  unsigned long long* base;
-  unsigned int* fill;
+  Slot* slots;
   unsigned long long mask;  // slots - 1
 };
 
 __device__ long long table_insert(const TableRef& t, unsigned long long key, CandState* st) {
   unsigned long long s = mix64(key) & t.mask;
   for (int i = 0; i < kMaxProbe; ++i) {
-    const unsigned long long cur = t.keys[s];
+    const unsigned long long cur = t.slots[s].key;
     if (cur == key) return (long long)s;
     if (cur == kEmptyKey) {
-      const unsigned long long prev = atomicCAS(t.keys + s, kEmptyKey, key);
+      const unsigned long long prev = atomicCAS(&t.slots[s].key, kEmptyKey, key);
       if (prev == kEmptyKey || prev == key) return (long long)s;
     }
     s = (s + 1) & t.mask;
@@ -146,7 +154,7 @@ __device__ long long table_insert(const TableRef& t, unsigned long long key, Can
 __device__ long long table_find(const TableRef& t, unsigned long long key) {
   unsigned long long s = mix64(key) & t.mask;
   for (int i = 0; i < kMaxProbe; ++i) {
-    const unsigned long long cur = t.keys[s];
+    const unsigned long long cur = t.slots[s].key;
     if (cur == key) return (long long)s;
     if (cur == kEmptyKey) return -1;
     s = (s + 1) & t.mask;
@@ -165,7 +173,7 @@ struct StoreRef {
 // Pass 1 (count) and pass 3 (fill) share the walk over every k-mer occurrence.
 template <bool kFill>
 __global__ void kmer_walk_kernel(StoreRef sr, TableRef t, unsigned long long* inst, unsigned long long inst_cap,
-                                 CandState* st) {
+                                 int mult_lo, int mult_hi, CandState* st) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -174,43 +182,60 @@ __global__ void kmer_walk_kernel(StoreRef sr, TableRef t, unsigned long long* in
     const long long first = sr.word_offsets[r] * 16;
     for (long long p = lane; p + sr.k <= len; p += 32) {
       unsigned orient;
-      const unsigned long long c = canonical(bases_le(sr.words, first + p, sr.k), sr.k, &orient);
+      const unsigned long long c = canonical(bases_le(sr.words, first + p, sr.k), sr.k, &orient) + 1ull;
       if (!kFill) {
         const long long s = table_insert(t, c, st);
-        if (s >= 0) atomicAdd(t.counts + s, 1u);
+        if (s >= 0) atomicAdd(&t.slots[s].count, 1u);
       } else {
         const long long s = table_find(t, c);
         if (s < 0) continue;
-        const unsigned long long b = t.base[s];
-        if (b == kNoBase) continue;
-        const unsigned slot = atomicAdd(t.fill + s, 1u);
-        if (b + slot >= inst_cap) {
+        const int cnt = (int)t.slots[s].count;
+        if (cnt < mult_lo || cnt > mult_hi) continue;
+        const unsigned long long at = atomicAdd(&t.slots[s].cursor, 1u);
+        if (at >= inst_cap) {
           atomicOr(&st->status, 8u);
           continue;
         }
-        inst[b + slot] = ((unsigned long long)r << 32) | ((unsigned long long)p << 1) | orient;
+        inst[at] = ((unsigned long long)r << 32) | ((unsigned long long)p << 1) | orient;
       }
     }
   }
 }
 
-// Pass 2: retained slots get their occurrence segment (warp-aggregated atomics;
-// every lane runs the same iterations).
+// Pass 2: retained slots get their occurrence segment.  Each lane takes
+// kAllocPerLane consecutive slots; one warp-aggregated atomic per counter
+// serves the warp's 32 x kAllocPerLane slots.
 __global__ void allocate_kernel(TableRef t, unsigned long long n_slots, int mult_lo, int mult_hi,
                                 unsigned int* retained_list, CandState* st) {
   const unsigned long long lane = threadIdx.x & 31;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n_slots;
-       w0 += stride) {
-    const unsigned long long s = w0 + lane;
-    const bool occ = s < n_slots && t.keys[s] != kEmptyKey;
-    const unsigned c = occ ? t.counts[s] : 0u;
-    const bool keep = occ && (int)c >= mult_lo && (int)c <= mult_hi;
-    warp_atomic_add(&st->instances, c);
-    const unsigned long long b = warp_atomic_add(&st->inst_cursor, keep ? c : 0u);
-    const unsigned long long r = warp_atomic_add(&st->retained, keep ? 1u : 0u);
-    if (occ) t.base[s] = keep ? b : kNoBase;
-    if (keep) retained_list[r] = (unsigned int)s;
+  constexpr unsigned long long kWarpSpan = 32ull * kAllocPerLane;
+  const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long w0 = warp * kWarpSpan; w0 < n_slots; w0 += n_warps * kWarpSpan) {
+    const unsigned long long s0 = w0 + lane * kAllocPerLane;
+    unsigned long long occ_sum = 0, keep_occ = 0, keep_n = 0;
+    for (int j = 0; j < kAllocPerLane; ++j) {
+      const unsigned long long s = s0 + j;
+      if (s >= n_slots || t.slots[s].key == kEmptyKey) continue;
+      const int c = (int)t.slots[s].count;
+      occ_sum += c;
+      if (c >= mult_lo && c <= mult_hi) {
+        keep_occ += c;
+        keep_n += 1;
+      }
+    }
+    warp_atomic_add(&st->instances, occ_sum);
+    unsigned long long b = warp_atomic_add(&st->inst_cursor, keep_occ);
+    unsigned long long r = warp_atomic_add(&st->retained, keep_n);
+    for (int j = 0; j < kAllocPerLane && keep_n; ++j) {
+      const unsigned long long s = s0 + j;
+      if (s >= n_slots || t.slots[s].key == kEmptyKey) continue;
+      const int c = (int)t.slots[s].count;
+      if (c < mult_lo || c > mult_hi) continue;
+      t.slots[s].cursor = (unsigned int)b;
+      retained_list[r++] = (unsigned int)s;
+      b += c;
+    }
   }
 }
 
@@ -228,8 +253,8 @@ __global__ void emit_pairs_kernel(TableRef t, const unsigned int* retained_list,
     int c = 0, n_pairs = 0;
     if (i < n) {
       const unsigned s = retained_list[i];
-      c = (int)t.counts[s];
-      const unsigned long long b = t.base[s];
+      c = (int)t.slots[s].count;
+      const unsigned long long b = (unsigned long long)t.slots[s].cursor - c;  // fill advanced it by c
       if (b + c > inst_cap) c = 0;  // its occurrences did not fit (status bit 3 is set)
       for (int x = 0; x < c; ++x) v[x] = inst[b + x];
       for (int x = 1; x < c; ++x) {  // insertion sort by (read, pos, orientation)
@@ -480,7 +505,7 @@ struct CandLayout {
   unsigned long long inst;   // occurrence capacity
   unsigned long long pairs;  // occurrence-pair capacity
   unsigned long long tiles;  // sort tiles
-  size_t state, keys, counts, base, fill, retained, inst_arr, pk0, pk1, hist, hoff, flags, sid, tsum, toff, total;
+  size_t state, table, retained, inst_arr, pk0, pk1, hist, hoff, flags, sid, tsum, toff, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -497,10 +522,7 @@ CandLayout cand_layout(long long n_bases, int k, int mult_hi) {
   (void)k;
   size_t off = 0;
   L.state = off;    off = align256(off + sizeof(CandState));
-  L.keys = off;     off = align256(off + 8 * slots);
-  L.counts = off;   off = align256(off + 4 * slots);
-  L.base = off;     off = align256(off + 8 * slots);
-  L.fill = off;     off = align256(off + 4 * slots);
+  L.table = off;    off = align256(off + sizeof(Slot) * slots);
   L.retained = off; off = align256(off + 4 * slots);
   L.inst_arr = off; off = align256(off + 8 * inst);
   L.pk0 = off;      off = align256(off + 8 * L.pairs);
@@ -537,6 +559,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
       pairs_capacity < 0 || !counts_out || !workspace || ((uintptr_t)workspace & 255))
     return DIBELLA_EINVAL;
   if (n_reads > 0 && (!packed_words || !read_word_offsets || !read_lengths)) return DIBELLA_EINVAL;
+  if (n_bases >= (int64_t)0xFFFFFFFFll) return DIBELLA_EINVAL;  // occurrence cursors are 32-bit
   if (pairs_capacity > 0 && !pairs_out) return DIBELLA_EINVAL;
   const int rbits = bits_for(n_reads > 0 ? (unsigned long long)(n_reads - 1) : 0);
   const int pbits = bits_for(max_read_len > 0 ? (unsigned long long)max_read_len : 0);
@@ -547,10 +570,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   char* ws = (char*)workspace;
   CandState* state = (CandState*)(ws + L.state);
   TableRef t;
-  t.keys = (unsigned long long*)(ws + L.keys);
-  t.counts = (unsigned int*)(ws + L.counts);
-  t.base = (unsigned long long*)(ws + L.base);
-  t.fill = (unsigned int*)(ws + L.fill);
+  t.slots = (Slot*)(ws + L.table);
   t.mask = L.slots - 1;
   unsigned int* retained = (unsigned int*)(ws + L.retained);
   unsigned long long* inst = (unsigned long long*)(ws + L.inst_arr);
@@ -573,9 +593,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
-  if ((e = cudaMemsetAsync(t.keys, 0xFF, 8 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
-  if ((e = cudaMemsetAsync(t.counts, 0, 4 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
-  if ((e = cudaMemsetAsync(t.fill, 0, 4 * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
+  if ((e = cudaMemsetAsync(t.slots, 0, sizeof(Slot) * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -583,9 +601,9 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   StoreRef sr{packed_words, read_word_offsets, read_lengths, (long long)n_reads, k};
   const int walk_blocks = sms * 16;
   if (n_reads > 0) {
-    kmer_walk_kernel<false><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, state);
+    kmer_walk_kernel<false><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, mult_lo, mult_hi, state);
     allocate_kernel<<<sms * 8, 256, 0, st>>>(t, L.slots, mult_lo, mult_hi, retained, state);
-    kmer_walk_kernel<true><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, state);
+    kmer_walk_kernel<true><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, mult_lo, mult_hi, state);
     emit_pairs_kernel<<<sms * 8, 256, 0, st>>>(t, retained, inst, L.inst, kl, pk0, L.pairs, state);
   }
   cap_keys_kernel<<<1, 1, 0, st>>>(state, L.pairs);
