@@ -465,7 +465,9 @@ def mode_candidates(args):
         "counts": {"seed_records": int(c[0]), "candidate_pairs": n_cand, "kmer_occurrences": int(c[2]),
                    "retained_kmers": int(c[3]), "occurrence_pairs": int(c[4])},
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                     "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     # profiles/candidate_pairs_c2_ecoli_launch_list.md: DRAM bytes of one call
+                     "traffic": 53061895629 if w.name == "c2_ecoli" else None,
                      "kernel": "whole call (count, allocate, fill, emit, %d radix passes, select, compact)"
                                % passes,
                      "peak_source": "%s hbm_gbs" % pk_kind,
