@@ -295,10 +295,10 @@ __global__ void cap_keys_kernel(CandState* st, unsigned long long capacity) {
 
 // ---- LSD radix sort of 64-bit keys (8-bit digits) ------------------------
 
-__global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, const CandState* st, int shift,
-                                  unsigned int* hist, unsigned long long n_tiles_max) {
+__global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, const unsigned long long* n_ptr,
+                                  int shift, unsigned int* hist, unsigned long long n_tiles_max) {
   __shared__ unsigned int h[256];
-  const unsigned long long n = st->n_keys;
+  const unsigned long long n = *n_ptr;
   const unsigned long long n_tiles = (n + kTile - 1) / kTile;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles && tile < n_tiles_max; tile += gridDim.x) {
     h[threadIdx.x] = 0;
@@ -314,13 +314,15 @@ __global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, c
   }
 }
 
-// Exclusive scan, in place, of len u32 counts into u64 offsets (one block).
-__global__ void scan_counts_kernel(const unsigned int* counts, unsigned long long* offsets, const CandState* st,
-                                   int per_digit, unsigned long long fixed_len) {
+// Exclusive scan of len u32 counts into u64 offsets (one block); len is
+// fixed_len, or from *n_ptr: 256 digit counts per tile (mode 1), one per tile
+// (mode 2).
+__global__ void scan_counts_kernel(const unsigned int* counts, unsigned long long* offsets,
+                                   const unsigned long long* n_ptr, int per_digit, unsigned long long fixed_len) {
   __shared__ unsigned long long part[kScanThreads];
   unsigned long long len = fixed_len;
-  if (per_digit == 1) len = 256ull * ((st->n_keys + kTile - 1) / kTile);
-  if (per_digit == 2) len = (st->n_keys + kTile - 1) / kTile;
+  if (per_digit == 1) len = 256ull * ((*n_ptr + kTile - 1) / kTile);
+  if (per_digit == 2) len = (*n_ptr + kTile - 1) / kTile;
   const unsigned long long chunk = (len + kScanThreads - 1) / kScanThreads;
   const unsigned long long lo = threadIdx.x * chunk;
   unsigned long long sum = 0;
@@ -345,12 +347,12 @@ __global__ void scan_counts_kernel(const unsigned int* counts, unsigned long lon
 }
 
 __global__ void digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
-                                     const CandState* st, int shift, const unsigned long long* offsets) {
+                                     const unsigned long long* n_ptr, int shift, const unsigned long long* offsets) {
   __shared__ unsigned long long base[256];
   __shared__ unsigned int wcnt[kSortThreads / 32][257];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const unsigned long long n = st->n_keys;
+  const unsigned long long n = *n_ptr;
   const unsigned long long n_tiles = (n + kTile - 1) / kTile;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     base[threadIdx.x] = offsets[(unsigned long long)threadIdx.x * n_tiles + tile];
@@ -380,6 +382,107 @@ __global__ void digit_scatter_kernel(const unsigned long long* __restrict__ in, 
       base[threadIdx.x] += tot;
       __syncthreads();
     }
+  }
+}
+
+// ---- sort-based count (when code and occurrence index share 64 bits) ----------
+
+__global__ void occ_count_kernel(StoreRef sr, unsigned int* cnt) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < sr.n_reads;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int len = sr.lengths[r];
+    cnt[r] = len >= sr.k ? (unsigned)(len - sr.k + 1) : 0u;
+  }
+}
+
+// The occurrence total; above the capacity (n_bases understated) it is capped
+// for the sort and status bit 3 marks the results incomplete.
+__global__ void occ_total_kernel(const unsigned int* cnt, const unsigned long long* off, long long n_reads,
+                                 unsigned long long cap, CandState* st) {
+  unsigned long long total = n_reads > 0 ? off[n_reads - 1] + cnt[n_reads - 1] : 0ull;
+  if (total > cap) {
+    total = cap;
+    st->status |= 8u;
+  }
+  st->instances = total;
+}
+
+// Every occurrence as (canonical code << ib | occurrence index), and its read,
+// position and orientation under that index.
+__global__ void extract_kernel(StoreRef sr, const unsigned long long* off, int ib, unsigned long long cap,
+                               unsigned long long* keys, unsigned long long* info) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = warp; r < sr.n_reads; r += n_warps) {
+    const long long len = sr.lengths[r];
+    const long long first = sr.word_offsets[r] * 16;
+    const unsigned long long o = off[r];
+    for (long long p = lane; p + sr.k <= len; p += 32) {
+      unsigned orient;
+      const unsigned long long c = canonical(bases_le(sr.words, first + p, sr.k), sr.k, &orient);
+      const unsigned long long idx = o + (unsigned long long)p;
+      if (idx >= cap) break;  // n_bases understated (status bit 3)
+      keys[idx] = (c << ib) | idx;
+      info[idx] = ((unsigned long long)r << 32) | ((unsigned long long)p << 1) | orient;
+    }
+  }
+}
+
+// A thread per run of equal codes in the sorted occurrences: the multiplicity,
+// and for a retained k-mer its occurrence pairs (as in emit_pairs_kernel).
+__global__ void run_emit_kernel(const unsigned long long* __restrict__ sorted, const unsigned long long* info, int ib,
+                                int mult_lo, int mult_hi, KeyLayout kl, unsigned long long* keys_out,
+                                unsigned long long capacity, CandState* st) {
+  const unsigned long long n = st->instances;
+  const unsigned long long imask = (1ull << ib) - 1ull;
+  const unsigned long long lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n;
+       w0 += stride) {
+    const unsigned long long i = w0 + lane;
+    bool keep = false;
+    int c = 0;
+    if (i < n && (i == 0 || (sorted[i - 1] >> ib) != (sorted[i] >> ib))) {
+      const unsigned long long code = sorted[i] >> ib;
+      unsigned long long e = i + 1;
+      while (e < n && (sorted[e] >> ib) == code && e - i <= (unsigned long long)mult_hi) ++e;
+      const unsigned long long mult = e - i;  // capped at mult_hi + 1: enough to reject
+      keep = mult >= (unsigned long long)mult_lo && mult <= (unsigned long long)mult_hi;
+      c = keep ? (int)mult : 0;
+    }
+    warp_atomic_add(&st->retained, keep ? 1u : 0u);
+    unsigned long long v[kMaxMult];
+    int n_pairs = 0;
+    if (keep) {
+      for (int x = 0; x < c; ++x) v[x] = info[sorted[i + x] & imask];
+      for (int x = 1; x < c; ++x) {
+        const unsigned long long t = v[x];
+        int y = x - 1;
+        while (y >= 0 && v[y] > t) {
+          v[y + 1] = v[y];
+          --y;
+        }
+        v[y + 1] = t;
+      }
+      for (int x = 0; x < c; ++x)
+        for (int y = x + 1; y < c; ++y) n_pairs += (v[x] >> 32) != (v[y] >> 32);
+    }
+    const unsigned long long at = warp_atomic_add(&st->occ_pairs, (unsigned long long)n_pairs);
+    if (n_pairs == 0) continue;
+    if (at + n_pairs > capacity) {
+      atomicOr(&st->status, 2u);
+      continue;
+    }
+    unsigned long long o = at;
+    for (int x = 0; x < c; ++x)
+      for (int y = x + 1; y < c; ++y) {
+        const unsigned long long ra = v[x] >> 32, rb = v[y] >> 32;
+        if (ra == rb) continue;
+        const unsigned long long pa = (v[x] >> 1) & 0x7FFFFFFFull, pb = (v[y] >> 1) & 0x7FFFFFFFull;
+        const unsigned long long strand = (v[x] ^ v[y]) & 1ull;
+        keys_out[o++] = (ra << kl.sh_ra) | (rb << kl.sh_rb) | (pa << kl.sh_pa) | (pb << kl.sh_pb) | strand;
+      }
   }
 }
 
@@ -500,31 +603,48 @@ int bits_for(unsigned long long v) {  // bits needed for values 0..v
   return b;
 }
 
+// The sort-based count keys each occurrence by (canonical code << ib |
+// occurrence index), ib = bits(n_bases): it applies while both fit 64 bits
+// (k = 17 up to 2^30 bases); otherwise the hash table counts.
+bool use_sort(long long n_bases, int k) { return 2 * k + bits_for(n_bases > 0 ? n_bases : 1) <= 64; }
+
 struct CandLayout {
-  unsigned long long slots;  // hash table slots (power of two)
+  bool sort;                 // sort-based count (else the hash table)
+  unsigned long long slots;  // hash table slots (power of two; 0 on the sort path)
   unsigned long long inst;   // occurrence capacity
   unsigned long long pairs;  // occurrence-pair capacity
-  unsigned long long tiles;  // sort tiles
-  size_t state, table, retained, inst_arr, pk0, pk1, hist, hoff, flags, sid, tsum, toff, total;
+  unsigned long long tiles;  // sort tiles (the larger of the two sorts)
+  size_t state, table, retained, inst_arr, occ_cnt, occ_off, okeys0, okeys1, info, pk0, pk1, hist, hoff, flags,
+      sid, tsum, toff, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-CandLayout cand_layout(long long n_bases, int k, int mult_hi) {
+CandLayout cand_layout(long long n_reads, long long n_bases, int k, int mult_hi) {
   CandLayout L;
   const unsigned long long inst = (unsigned long long)(n_bases > 0 ? n_bases : 1);
-  unsigned long long slots = 1024;
-  while (slots < inst + inst / 2) slots <<= 1;  // load factor below 2/3
+  const unsigned long long reads = (unsigned long long)(n_reads > 0 ? n_reads : 1);
+  L.sort = use_sort(n_bases, k);
+  unsigned long long slots = 0;
+  if (!L.sort) {
+    slots = 1024;
+    while (slots < inst + inst / 2) slots <<= 1;  // load factor below 2/3
+  }
   L.slots = slots;
   L.inst = inst;
   L.pairs = inst * (unsigned long long)(mult_hi > 1 ? mult_hi - 1 : 1) / 2 + 1;
-  L.tiles = (L.pairs + kTile - 1) / kTile;
-  (void)k;
+  const unsigned long long ptiles = (L.pairs + kTile - 1) / kTile, otiles = (inst + kTile - 1) / kTile;
+  L.tiles = ptiles > otiles ? ptiles : otiles;
   size_t off = 0;
   L.state = off;    off = align256(off + sizeof(CandState));
   L.table = off;    off = align256(off + sizeof(Slot) * slots);
   L.retained = off; off = align256(off + 4 * slots);
-  L.inst_arr = off; off = align256(off + 8 * inst);
+  L.inst_arr = off; off = align256(off + (L.sort ? 0 : 8 * inst));
+  L.occ_cnt = off;  off = align256(off + (L.sort ? 4 * reads : 0));
+  L.occ_off = off;  off = align256(off + (L.sort ? 8 * reads : 0));
+  L.okeys0 = off;   off = align256(off + (L.sort ? 8 * inst : 0));
+  L.okeys1 = off;   off = align256(off + (L.sort ? 8 * inst : 0));
+  L.info = off;     off = align256(off + (L.sort ? 8 * inst : 0));
   L.pk0 = off;      off = align256(off + 8 * L.pairs);
   L.pk1 = off;      off = align256(off + 8 * L.pairs);
   L.hist = off;     off = align256(off + 4 * 256 * L.tiles);
@@ -545,7 +665,7 @@ int dibella_candidate_workspace_bytes(int64_t n_reads, int64_t n_bases, int32_t 
                                       int64_t* bytes_out) {
   if (!bytes_out || n_reads < 0 || n_bases < 0 || k < 1 || k > 32 || mult_hi < 1 || mult_hi > kMaxMult)
     return DIBELLA_EINVAL;
-  *bytes_out = (int64_t)cand_layout(n_bases, k, mult_hi).total;
+  *bytes_out = (int64_t)cand_layout(n_reads, n_bases, k, mult_hi).total;
   return DIBELLA_OK;
 }
 
@@ -564,7 +684,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   const int rbits = bits_for(n_reads > 0 ? (unsigned long long)(n_reads - 1) : 0);
   const int pbits = bits_for(max_read_len > 0 ? (unsigned long long)max_read_len : 0);
   if (2 * rbits + 2 * pbits + 1 > 64) return DIBELLA_EINVAL;
-  const CandLayout L = cand_layout(n_bases, k, mult_hi);
+  const CandLayout L = cand_layout(n_reads, n_bases, k, mult_hi);
   if ((unsigned long long)workspace_bytes < L.total) return DIBELLA_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
@@ -593,14 +713,40 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
-  if ((e = cudaMemsetAsync(t.slots, 0, sizeof(Slot) * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
+  if (!L.sort && (e = cudaMemsetAsync(t.slots, 0, sizeof(Slot) * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 1;
   StoreRef sr{packed_words, read_word_offsets, read_lengths, (long long)n_reads, k};
   const int walk_blocks = sms * 16;
-  if (n_reads > 0) {
+  const int sort_blocks = sms * 8;
+  if (n_reads > 0 && L.sort) {
+    // Occurrence keys (code << ib | index), sorted by the code digits only: the
+    // stable passes keep each k-mer's occurrences in index order.
+    unsigned int* occ_cnt = (unsigned int*)(ws + L.occ_cnt);
+    unsigned long long* occ_off = (unsigned long long*)(ws + L.occ_off);
+    unsigned long long* ok0 = (unsigned long long*)(ws + L.okeys0);
+    unsigned long long* ok1 = (unsigned long long*)(ws + L.okeys1);
+    unsigned long long* info = (unsigned long long*)(ws + L.info);
+    const int ib = bits_for((unsigned long long)n_bases);
+    occ_count_kernel<<<sms * 4, 256, 0, st>>>(sr, occ_cnt);
+    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(occ_cnt, occ_off, &state->instances, 0,
+                                                   (unsigned long long)n_reads);
+    occ_total_kernel<<<1, 1, 0, st>>>(occ_cnt, occ_off, (long long)n_reads, L.inst, state);
+    extract_kernel<<<walk_blocks, 256, 0, st>>>(sr, occ_off, ib, L.inst, ok0, info);
+    unsigned long long* osrc = ok0;
+    unsigned long long* odst = ok1;
+    for (int j = 0; j < (2 * k + 7) / 8; ++j) {
+      digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(osrc, &state->instances, ib + 8 * j, hist, L.tiles);
+      scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, &state->instances, 1, 0);
+      digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(osrc, odst, &state->instances, ib + 8 * j, hoff);
+      unsigned long long* tmp = osrc;
+      osrc = odst;
+      odst = tmp;
+    }
+    run_emit_kernel<<<sms * 8, 256, 0, st>>>(osrc, info, ib, mult_lo, mult_hi, kl, pk0, L.pairs, state);
+  } else if (n_reads > 0) {
     kmer_walk_kernel<false><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, mult_lo, mult_hi, state);
     allocate_kernel<<<sms * 8, 256, 0, st>>>(t, L.slots, mult_lo, mult_hi, retained, state);
     kmer_walk_kernel<true><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, mult_lo, mult_hi, state);
@@ -612,18 +758,17 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   const int passes = (key_bits + 7) / 8;
   unsigned long long* src = pk0;
   unsigned long long* dst = pk1;
-  const int sort_blocks = sms * 8;
   for (int pss = 0; pss < passes; ++pss) {
-    digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, state, 8 * pss, hist, L.tiles);
-    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, state, 1, 0);
-    digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, dst, state, 8 * pss, hoff);
+    digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, &state->n_keys, 8 * pss, hist, L.tiles);
+    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, &state->n_keys, 1, 0);
+    digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, dst, &state->n_keys, 8 * pss, hoff);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
   }
   select_kernel<<<sms * 8, 256, 0, st>>>(src, state, kl, max_seeds, min_seed_gap > 0 ? min_seed_gap : k, flags, sid);
   tile_sum_kernel<<<sort_blocks, kSortThreads, 0, st>>>(flags, state, tsum);
-  scan_counts_kernel<<<1, kScanThreads, 0, st>>>(tsum, toff, state, 2, 0);
+  scan_counts_kernel<<<1, kScanThreads, 0, st>>>(tsum, toff, &state->n_keys, 2, 0);
   compact_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, flags, sid, toff, state, kl, pairs_out,
                                                          (unsigned long long)pairs_capacity);
   finish_kernel<<<1, 1, 0, st>>>(state, toff, tsum, counts_out);
