@@ -308,7 +308,8 @@ int dibella_candidate_workspace_bytes(int64_t n_reads, int64_t n_bases, int32_t 
  * candidate pairs, k-mer occurrences, retained k-mers, occurrence pairs,
  * status}; status 0 = complete, else bit 0 the hash table filled, bit 1 more
  * occurrence pairs than the workspace holds, bit 2 more seed records than
- * pairs_capacity, bit 3 more occurrences than n_bases (the records are then
+ * pairs_capacity, bit 3 more occurrences than n_bases, bit 4 a radix pass
+ * whose counts disagreed with its histogram (the records are then
  * incomplete).  Synchronous EINVAL: k outside 1..32, 1 <= mult_lo <= mult_hi
  * <= 32 violated, max_seeds < 1, min_seed_gap < 0, max_read_len outside
  * 0..DIBELLA_MAX_READ_LEN, null or misaligned buffers, or read and position

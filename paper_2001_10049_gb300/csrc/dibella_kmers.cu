@@ -48,7 +48,8 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr unsigned long long kEmptyKey = 0ull;  // slots hold canonical code + 1 (see canonical)
 constexpr int kMaxProbe = 1 << 14;
 constexpr int kMaxMult = 32;
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 1024;  // 32 warps: block_sum and the warp-total scan rely on it
+constexpr int kScanBlocks = 256;    // at most kScanThreads
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 64;
 constexpr int kAllocPerLane = 16;
@@ -64,7 +65,7 @@ struct CandState {
   unsigned long long candidates;  // distinct (read_a, read_b)
   unsigned long long seeds;       // seed records written
   unsigned int status;            // bit 0 table full, bit 1 pair capacity, bit 2 output
-                                  // capacity, bit 3 occurrence capacity
+                                  // capacity, bit 3 occurrence capacity, bit 4 sort inconsistency
   unsigned int pad;
 };
 
@@ -314,74 +315,198 @@ __global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, c
   }
 }
 
-// Exclusive scan of len u32 counts into u64 offsets (one block); len is
-// fixed_len, or from *n_ptr: 256 digit counts per tile (mode 1), one per tile
-// (mode 2).
-__global__ void scan_counts_kernel(const unsigned int* counts, unsigned long long* offsets,
-                                   const unsigned long long* n_ptr, int per_digit, unsigned long long fixed_len) {
-  __shared__ unsigned long long part[kScanThreads];
-  unsigned long long len = fixed_len;
-  if (per_digit == 1) len = 256ull * ((*n_ptr + kTile - 1) / kTile);
-  if (per_digit == 2) len = (*n_ptr + kTile - 1) / kTile;
-  const unsigned long long chunk = (len + kScanThreads - 1) / kScanThreads;
-  const unsigned long long lo = threadIdx.x * chunk;
-  unsigned long long sum = 0;
-  for (unsigned long long i = lo; i < lo + chunk && i < len; ++i) sum += counts[i];
-  part[threadIdx.x] = sum;
+// Exclusive scan of len u32 counts into u64 offsets; len is fixed_len, or from
+// *n_ptr: 256 digit counts per tile (mode 1), one per tile (mode 2).  Two
+// launches of kScanBlocks blocks: each block sums its contiguous segment
+// (scan_reduce_kernel), then scans it from the sum of the segments before it
+// (scan_apply_kernel).  Both read the counts coalesced.
+__device__ __forceinline__ unsigned long long scan_len(const unsigned long long* n_ptr, int mode,
+                                                       unsigned long long fixed_len) {
+  if (mode == 1) return 256ull * ((*n_ptr + kTile - 1) / kTile);
+  if (mode == 2) return (*n_ptr + kTile - 1) / kTile;
+  return fixed_len;
+}
+
+// Sum over the block (kScanThreads threads); every thread gets the result.
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long* wsum) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long acc = 0;
-    for (int i = 0; i < kScanThreads; ++i) {
-      const unsigned long long v = part[i];
-      part[i] = acc;
-      acc += v;
+  v = wsum[threadIdx.x & 31];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const unsigned int* counts,
+                                                                   const unsigned long long* n_ptr, int mode,
+                                                                   unsigned long long fixed_len,
+                                                                   unsigned long long* part) {
+  __shared__ unsigned long long wsum[32];
+  const unsigned long long len = scan_len(n_ptr, mode, fixed_len);
+  const unsigned long long seg = (len + gridDim.x - 1) / gridDim.x;
+  const unsigned long long lo = blockIdx.x * seg;
+  const unsigned long long hi = lo + seg < len ? lo + seg : len;
+  unsigned long long s = 0;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += kScanThreads) s += counts[i];
+  s = block_sum(s, wsum);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const unsigned int* counts,
+                                                                  unsigned long long* offsets,
+                                                                  const unsigned long long* n_ptr, int mode,
+                                                                  unsigned long long fixed_len,
+                                                                  const unsigned long long* part) {
+  __shared__ unsigned long long wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long len = scan_len(n_ptr, mode, fixed_len);
+  const unsigned long long seg = (len + gridDim.x - 1) / gridDim.x;
+  const unsigned long long lo = blockIdx.x * seg;
+  const unsigned long long hi = lo + seg < len ? lo + seg : len;
+  // gridDim.x <= kScanThreads: thread t holds the sum of segment t.
+  unsigned long long base = block_sum(threadIdx.x < blockIdx.x ? part[threadIdx.x] : 0ull, wsum);
+  for (unsigned long long c = lo; c < hi; c += kScanThreads) {  // uniform over the block
+    const unsigned long long i = c + threadIdx.x;
+    const unsigned long long v = i < hi ? counts[i] : 0ull;
+    unsigned long long x = v;  // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFullMask, x, o);
+      if (lane >= o) x += y;
     }
-  }
-  __syncthreads();
-  unsigned long long acc = part[threadIdx.x];
-  for (unsigned long long i = lo; i < lo + chunk && i < len; ++i) {
-    const unsigned long long v = counts[i];
-    offsets[i] = acc;
-    acc += v;
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {  // inclusive scan of the 32 warp totals
+      unsigned long long w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFullMask, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    if (i < hi) offsets[i] = base + (warp > 0 ? wsum[warp - 1] : 0ull) + x - v;
+    base += wsum[31];
+    __syncthreads();
   }
 }
 
-__global__ void digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
-                                     const unsigned long long* n_ptr, int shift, const unsigned long long* offsets) {
-  __shared__ unsigned long long base[256];
-  __shared__ unsigned int wcnt[kSortThreads / 32][257];
+void scan_counts(const unsigned int* counts, unsigned long long* offsets, const unsigned long long* n_ptr, int mode,
+                 unsigned long long fixed_len, unsigned long long* part, cudaStream_t st) {
+  scan_reduce_kernel<<<kScanBlocks, kScanThreads, 0, st>>>(counts, n_ptr, mode, fixed_len, part);
+  scan_apply_kernel<<<kScanBlocks, kScanThreads, 0, st>>>(counts, offsets, n_ptr, mode, fixed_len, part);
+}
+
+// One stable pass of the LSD sort, a tile of kTile keys per block iteration:
+// the tile is copied into shared memory (16-byte asynchronous copies), each
+// warp ranks its contiguous kWarpKeys keys by digit (counts, then a prefix over
+// warps and digits, then ranks in input order), the permutation that sorts the
+// tile by digit is built in shared memory, and the tile is written out in that
+// order so that each digit's keys go to consecutive addresses.  A destination
+// outside [0, n) (counts that disagree with the histogram) is skipped and
+// flagged in status bit 4.
+constexpr int kScatterThreads = 512;
+constexpr int kScatterWarps = kScatterThreads / 32;
+constexpr int kWarpKeys = kTile / kScatterWarps;
+constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 2 + (size_t)kScatterWarps * 256 * 4 + 256 * 8 +
+                                256 * 4;
+static_assert(kTile <= 65536, "tile indices are 16-bit");
+static_assert(kScatterSmem <= 227 * 1024, "scatter tile does not fit shared memory");
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, unsigned src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem_src), "r"(src_bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kScatterThreads, 1)
+    digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
+                         const unsigned long long* n_ptr, int shift, const unsigned long long* offsets,
+                         unsigned int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* skey = (unsigned long long*)smem;                           // the tile, input order
+  unsigned short* inv = (unsigned short*)(smem + (size_t)kTile * 8);             // sorted slot -> input index
+  unsigned int* wcnt = (unsigned int*)(smem + (size_t)kTile * 10);               // [warp][digit]
+  unsigned long long* gbase = (unsigned long long*)(wcnt + kScatterWarps * 256);  // digit's first output slot
+  unsigned int* lstart = (unsigned int*)(gbase + 256);                           // digit's first slot in the tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const unsigned long long n = *n_ptr;
   const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  const int w0 = warp * kWarpKeys;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    base[threadIdx.x] = offsets[(unsigned long long)threadIdx.x * n_tiles + tile];
-    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
-    __syncthreads();
     const unsigned long long t0 = tile * kTile;
-    for (int j = 0; j < kSortItems; ++j) {
-      const unsigned long long i = t0 + (unsigned long long)j * kSortThreads + threadIdx.x;
-      const bool ok = i < n;
-      const unsigned long long key = ok ? in[i] : 0ull;
-      const unsigned d = ok ? (unsigned)((key >> shift) & 255u) : 256u;
+    const int m = n - t0 < (unsigned long long)kTile ? (int)(n - t0) : kTile;
+    for (int c = threadIdx.x; c < kTile / 2; c += kScatterThreads) {
+      const int e = 2 * c;  // a 16-byte chunk: keys e and e + 1, zero-filled past the tile's end
+      const unsigned bytes = e >= m ? 0u : (e + 1 < m ? 16u : 8u);
+      cp_async16(skey + e, bytes ? (const void*)(in + t0 + e) : (const void*)in, bytes);
+    }
+    for (int x = threadIdx.x; x < kScatterWarps * 256; x += kScatterThreads) wcnt[x] = 0;
+    cp_async_wait_all();
+    __syncthreads();
+    for (int r = 0; r < kWarpKeys; r += 32) {
+      const int i = w0 + r + lane;
+      if (i < m) atomicAdd(&wcnt[warp * 256 + (unsigned)((skey[i] >> shift) & 255u)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {  // thread d: prefix of digit d over the warps, and its tile count
+      unsigned tot = 0;
+      for (int w = 0; w < kScatterWarps; ++w) {
+        const unsigned v = wcnt[w * 256 + threadIdx.x];
+        wcnt[w * 256 + threadIdx.x] = tot;
+        tot += v;
+      }
+      lstart[threadIdx.x] = tot;
+      gbase[threadIdx.x] = offsets[(unsigned long long)threadIdx.x * n_tiles + tile];
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 256 tile counts, 8 digits per lane
+      unsigned v[8], sum = 0;
+      for (int q = 0; q < 8; ++q) {
+        v[q] = lstart[lane * 8 + q];
+        sum += v[q];
+      }
+      unsigned x = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFullMask, x, o);
+        if (lane >= o) x += y;
+      }
+      unsigned acc = x - sum;
+      for (int q = 0; q < 8; ++q) {
+        lstart[lane * 8 + q] = acc;
+        acc += v[q];
+      }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < kScatterWarps * 256; x += kScatterThreads) wcnt[x] += lstart[x & 255];
+    __syncthreads();
+    unsigned int* next = wcnt + warp * 256;  // this warp's next slot per digit
+    for (int r = 0; r < kWarpKeys; r += 32) {
+      const int i = w0 + r + lane;
+      const bool ok = i < m;
+      const unsigned d = ok ? (unsigned)((skey[i] >> shift) & 255u) : 256u;
       const unsigned peers = __match_any_sync(kFullMask, d);
       const unsigned rank = __popc(peers & lt);
-      if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
-      __syncthreads();
-      if (ok) {
-        unsigned long long pos = base[d] + rank;
-        for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-        out[pos] = key;
-      }
-      __syncthreads();
-      unsigned tot = 0;
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        tot += wcnt[w][threadIdx.x];
-        wcnt[w][threadIdx.x] = 0;
-      }
-      base[threadIdx.x] += tot;
-      __syncthreads();
+      const unsigned c = ok ? next[d] : 0u;
+      __syncwarp();
+      if (ok && rank == 0) next[d] = c + __popc(peers);
+      __syncwarp();
+      if (ok && c + rank < (unsigned)kTile) inv[c + rank] = (unsigned short)i;
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += kScatterThreads) {
+      const unsigned long long key = skey[inv[q] & (kTile - 1)];
+      const unsigned d = (unsigned)((key >> shift) & 255u);
+      const unsigned long long g = gbase[d] + (unsigned long long)(q - (int)lstart[d]);
+      if (g < n)
+        out[g] = key;
+      else
+        atomicOr(status, 16u);
+    }
+    __syncthreads();  // the next tile reuses shared memory
   }
 }
 
@@ -615,7 +740,7 @@ struct CandLayout {
   unsigned long long pairs;  // occurrence-pair capacity
   unsigned long long tiles;  // sort tiles (the larger of the two sorts)
   size_t state, table, retained, inst_arr, occ_cnt, occ_off, okeys0, okeys1, info, pk0, pk1, hist, hoff, flags,
-      sid, tsum, toff, total;
+      sid, tsum, toff, part, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -653,6 +778,7 @@ CandLayout cand_layout(long long n_reads, long long n_bases, int k, int mult_hi)
   L.sid = off;      off = align256(off + 4 * L.pairs);
   L.tsum = off;     off = align256(off + 4 * L.tiles);
   L.toff = off;     off = align256(off + 8 * L.tiles);
+  L.part = off;     off = align256(off + 8 * kScanBlocks);
   L.total = off;
   return L;
 }
@@ -702,6 +828,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   unsigned int* sid = (unsigned int*)(ws + L.sid);
   unsigned int* tsum = (unsigned int*)(ws + L.tsum);
   unsigned long long* toff = (unsigned long long*)(ws + L.toff);
+  unsigned long long* part = (unsigned long long*)(ws + L.part);
 
   KeyLayout kl;
   kl.sh_pb = 1;
@@ -712,6 +839,9 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   kl.m_pos = (1ull << pbits) - 1ull;
 
   cudaError_t e;
+  if ((e = cudaFuncSetAttribute(digit_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kScatterSmem)) != cudaSuccess)
+    return DIBELLA_ECUDA;
   if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
   if (!L.sort && (e = cudaMemsetAsync(t.slots, 0, sizeof(Slot) * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
   int dev = 0, sms = 0;
@@ -731,16 +861,16 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
     unsigned long long* info = (unsigned long long*)(ws + L.info);
     const int ib = bits_for((unsigned long long)n_bases);
     occ_count_kernel<<<sms * 4, 256, 0, st>>>(sr, occ_cnt);
-    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(occ_cnt, occ_off, &state->instances, 0,
-                                                   (unsigned long long)n_reads);
+    scan_counts(occ_cnt, occ_off, &state->instances, 0, (unsigned long long)n_reads, part, st);
     occ_total_kernel<<<1, 1, 0, st>>>(occ_cnt, occ_off, (long long)n_reads, L.inst, state);
     extract_kernel<<<walk_blocks, 256, 0, st>>>(sr, occ_off, ib, L.inst, ok0, info);
     unsigned long long* osrc = ok0;
     unsigned long long* odst = ok1;
     for (int j = 0; j < (2 * k + 7) / 8; ++j) {
       digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(osrc, &state->instances, ib + 8 * j, hist, L.tiles);
-      scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, &state->instances, 1, 0);
-      digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(osrc, odst, &state->instances, ib + 8 * j, hoff);
+      scan_counts(hist, hoff, &state->instances, 1, 0, part, st);
+      digit_scatter_kernel<<<sms, kScatterThreads, kScatterSmem, st>>>(osrc, odst, &state->instances, ib + 8 * j,
+                                                                       hoff, &state->status);
       unsigned long long* tmp = osrc;
       osrc = odst;
       odst = tmp;
@@ -760,15 +890,16 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   unsigned long long* dst = pk1;
   for (int pss = 0; pss < passes; ++pss) {
     digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, &state->n_keys, 8 * pss, hist, L.tiles);
-    scan_counts_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, &state->n_keys, 1, 0);
-    digit_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, dst, &state->n_keys, 8 * pss, hoff);
+    scan_counts(hist, hoff, &state->n_keys, 1, 0, part, st);
+    digit_scatter_kernel<<<sms, kScatterThreads, kScatterSmem, st>>>(src, dst, &state->n_keys, 8 * pss, hoff,
+                                                                     &state->status);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
   }
   select_kernel<<<sms * 8, 256, 0, st>>>(src, state, kl, max_seeds, min_seed_gap > 0 ? min_seed_gap : k, flags, sid);
   tile_sum_kernel<<<sort_blocks, kSortThreads, 0, st>>>(flags, state, tsum);
-  scan_counts_kernel<<<1, kScanThreads, 0, st>>>(tsum, toff, &state->n_keys, 2, 0);
+  scan_counts(tsum, toff, &state->n_keys, 2, 0, part, st);
   compact_kernel<<<sort_blocks, kSortThreads, 0, st>>>(src, flags, sid, toff, state, kl, pairs_out,
                                                          (unsigned long long)pairs_capacity);
   finish_kernel<<<1, 1, 0, st>>>(state, toff, tsum, counts_out);
