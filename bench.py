@@ -380,15 +380,26 @@ def mode_stream(args):
     }))
 
 
-# Algorithmic DRAM bytes of candidate generation: per k-mer occurrence, two
-# walks each touching one 8-byte table key and one 4-byte counter (plus the
-# 2-bit sequence, 0.5 B); per occurrence pair, the 8-byte key written once,
-# read and written by each 8-bit radix pass, read by selection and compaction.
-CAND_BYTES_PER_OCC = 24.5
+# Algorithmic DRAM bytes of candidate generation.  Sort-based count (code and
+# occurrence index share one 64-bit key): per k-mer occurrence, the 2-bit
+# sequence (0.5 B), the key and its (read, position, orientation) word written
+# (16 B), each 8-bit pass over the code digits reading the key for the
+# histogram and reading and writing it in the scatter (24 B), and the run walk
+# reading the key and gathering the word (16 B).  Hash-table count (wider
+# keys): two walks each touching one 8-byte table key and one 4-byte counter,
+# plus the sequence (24.5 B).  Per occurrence pair: the 8-byte key written,
+# 24 B per pass of its sort, read by selection and compaction (16 B).
+def cand_bytes_per_occ(sort_count: bool, k: int) -> float:
+    return 32.5 + 24 * ((2 * k + 7) // 8) if sort_count else 24.5
 
 
 def cand_bytes_per_pair(passes: int) -> int:
-    return 8 + 16 * passes + 16
+    return 8 + 24 * passes + 16
+
+
+# profiles/candidate_pairs_c2_ecoli_launch_list.md: DRAM bytes of one call
+# (every kernel of the call, from one ncu launch list).
+CAND_NCU_TRAFFIC = {"c2_ecoli": 25658249318}
 
 
 def mode_candidates(args):
@@ -440,7 +451,9 @@ def mode_candidates(args):
     rbits = max(1, int(store.n_reads - 1).bit_length())
     pbits = max(1, int(store.max_len).bit_length())
     passes = (2 * rbits + 2 * pbits + 1 + 7) // 8
-    alg = CAND_BYTES_PER_OCC * int(c[2]) + cand_bytes_per_pair(passes) * int(c[4])
+    sort_count = 2 * p["k"] + max(1, int(store.n_bases).bit_length()) <= 64
+    per_occ = cand_bytes_per_occ(sort_count, p["k"])
+    alg = per_occ * int(c[2]) + cand_bytes_per_pair(passes) * int(c[4])
     n_cand = int(c[1])
     cpu = None
     if not args.no_cpu:
@@ -466,13 +479,13 @@ def mode_candidates(args):
                    "retained_kmers": int(c[3]), "occurrence_pairs": int(c[4])},
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                     # profiles/candidate_pairs_c2_ecoli_launch_list.md: DRAM bytes of one call
-                     "traffic": 53061895629 if w.name == "c2_ecoli" else None,
-                     "kernel": "whole call (count, allocate, fill, emit, %d radix passes, select, compact)"
-                               % passes,
+                     "traffic": CAND_NCU_TRAFFIC.get(w.name),
+                     "kernel": ("whole call (occurrence keys, %d radix passes by code, run walk, %d radix passes"
+                                " of the pairs, select, compact)" % ((2 * p["k"] + 7) // 8, passes)) if sort_count
+                     else "whole call (count, allocate, fill, emit, %d radix passes, select, compact)" % passes,
                      "peak_source": "%s hbm_gbs" % pk_kind,
                      "bytes_model": "%.1f B per k-mer occurrence + %d B per occurrence pair"
-                                    % (CAND_BYTES_PER_OCC, cand_bytes_per_pair(passes))},
+                                    % (per_occ, cand_bytes_per_pair(passes))},
         "matches_generator": True,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
