@@ -51,7 +51,7 @@ constexpr int kMaxMult = 32;
 constexpr int kScanThreads = 1024;  // 32 warps: block_sum and the warp-total scan rely on it
 constexpr int kScanBlocks = 256;    // at most kScanThreads
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 64;
+constexpr int kSortItems = 32;
 constexpr int kAllocPerLane = 16;
 constexpr int kTile = kSortThreads * kSortItems;  // keys per sort / scan tile
 
@@ -405,13 +405,14 @@ void scan_counts(const unsigned int* counts, unsigned long long* offsets, const 
 // order so that each digit's keys go to consecutive addresses.  A destination
 // outside [0, n) (counts that disagree with the histogram) is skipped and
 // flagged in status bit 4.
-constexpr int kScatterThreads = 512;
+constexpr int kScatterThreads = 256;
+constexpr int kScatterBlocksPerSM = 2;
 constexpr int kScatterWarps = kScatterThreads / 32;
 constexpr int kWarpKeys = kTile / kScatterWarps;
 constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 2 + (size_t)kScatterWarps * 256 * 4 + 256 * 8 +
                                 256 * 4;
 static_assert(kTile <= 65536, "tile indices are 16-bit");
-static_assert(kScatterSmem <= 227 * 1024, "scatter tile does not fit shared memory");
+static_assert(kScatterBlocksPerSM * (kScatterSmem + 1024) <= 228 * 1024, "scatter tiles do not fit shared memory");
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, unsigned src_bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -421,7 +422,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src,
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(kScatterThreads, 1)
+__global__ void __launch_bounds__(kScatterThreads, kScatterBlocksPerSM)
     digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
                          const unsigned long long* n_ptr, int shift, const unsigned long long* offsets,
                          unsigned int* status) {
@@ -869,8 +870,8 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
     for (int j = 0; j < (2 * k + 7) / 8; ++j) {
       digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(osrc, &state->instances, ib + 8 * j, hist, L.tiles);
       scan_counts(hist, hoff, &state->instances, 1, 0, part, st);
-      digit_scatter_kernel<<<sms, kScatterThreads, kScatterSmem, st>>>(osrc, odst, &state->instances, ib + 8 * j,
-                                                                       hoff, &state->status);
+      digit_scatter_kernel<<<sms * kScatterBlocksPerSM, kScatterThreads, kScatterSmem, st>>>(
+          osrc, odst, &state->instances, ib + 8 * j, hoff, &state->status);
       unsigned long long* tmp = osrc;
       osrc = odst;
       odst = tmp;
@@ -891,8 +892,8 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   for (int pss = 0; pss < passes; ++pss) {
     digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, &state->n_keys, 8 * pss, hist, L.tiles);
     scan_counts(hist, hoff, &state->n_keys, 1, 0, part, st);
-    digit_scatter_kernel<<<sms, kScatterThreads, kScatterSmem, st>>>(src, dst, &state->n_keys, 8 * pss, hoff,
-                                                                     &state->status);
+    digit_scatter_kernel<<<sms * kScatterBlocksPerSM, kScatterThreads, kScatterSmem, st>>>(
+        src, dst, &state->n_keys, 8 * pss, hoff, &state->status);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
