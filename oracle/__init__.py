@@ -66,6 +66,11 @@ def _load():
         lib.oracle_align_one.restype = i32
         lib.oracle_xdrop_batch.argtypes = [vp, vp, i64, vp, i64, i32, i32, i32, i32, i32, vp, i32]
         lib.oracle_xdrop_batch.restype = i32
+        lib.oracle_extend_columns.argtypes = [cp, i64, cp, i64, i32, i32, i32, i32, vp, i64]
+        lib.oracle_extend_columns.restype = i64
+        lib.oracle_traceback_batch.argtypes = [vp, vp, i64, vp, i64, i32, i32, i32, i32, i32, vp, vp, i64,
+                                               vp]
+        lib.oracle_traceback_batch.restype = i32
         _lib = lib
     return _lib
 
@@ -125,3 +130,47 @@ def xdrop_batch(ascii: np.ndarray, offsets: np.ndarray, pairs: np.ndarray, k: in
     if rc != 0:
         raise ValueError("oracle_xdrop_batch rejected its arguments (rc=%d)" % rc)
     return out
+
+
+# SAM/BAM op numbers of the run-length encoded traceback words (run << 4 | op).
+CIGAR_OPS = {7: "=", 8: "X", 1: "I", 2: "D"}
+
+
+def extend_columns(a: str | bytes, b: str | bytes, match: int, mismatch: int, gap: int,
+                   xdrop: int) -> str:
+    """Columns of one extension's best alignment from the origin on: '=' equal
+    pair, 'X' unequal pair, 'D' a character of a only, 'I' a character of b only."""
+    a = a.encode() if isinstance(a, str) else a
+    b = b.encode() if isinstance(b, str) else b
+    cap = len(a) + len(b) + 1
+    buf = ctypes.create_string_buffer(cap)
+    n = _load().oracle_extend_columns(a, len(a), b, len(b), match, mismatch, gap, xdrop, buf, cap)
+    if n < 0:
+        raise RuntimeError("oracle traceback failed")
+    return buf.raw[:n].decode()
+
+
+def cigar_string(words) -> str:
+    """Text form of run-length encoded traceback words, e.g. '12=1X3=1D'."""
+    return "".join("%d%s" % (int(w) >> 4, CIGAR_OPS[int(w) & 15]) for w in words)
+
+
+def traceback_batch(ascii: np.ndarray, offsets: np.ndarray, pairs: np.ndarray, k: int, match: int,
+                    mismatch: int, gap: int, xdrop: int, cap_per_seed: int):
+    """Every seed's result (no best-of-pair flag) and its run-length encoded
+    columns: (results, ops[n, cap_per_seed] uint32, n_ops[n] int32 with -1 when
+    more than cap_per_seed runs were needed)."""
+    ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=PAIR_DTYPE)
+    res = np.zeros(len(pairs), dtype=RESULT_DTYPE)
+    ops = np.zeros((len(pairs), max(cap_per_seed, 1)), dtype=np.uint32)
+    n_ops = np.zeros(len(pairs), dtype=np.int32)
+    rc = _load().oracle_traceback_batch(
+        ascii.ctypes.data_as(ctypes.c_void_p), offsets.ctypes.data_as(ctypes.c_void_p),
+        len(offsets) - 1, pairs.ctypes.data_as(ctypes.c_void_p), len(pairs), k, match, mismatch, gap,
+        xdrop, res.ctypes.data_as(ctypes.c_void_p), ops.ctypes.data_as(ctypes.c_void_p), ops.shape[1],
+        n_ops.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError("oracle_traceback_batch failed (rc=%d)" % rc)
+    return res, ops, n_ops

@@ -26,13 +26,22 @@
 //       antidiagonal the live cell of smallest i wins;
 //   R4  `cells` counts every evaluated cell on antidiagonals d >= 1;
 //   R5  seeded score = seed score + left best + right best, half-open
-//       coordinates, read B reported in forward coordinates.
+//       coordinates, read B reported in forward coordinates;
+//   R12 the traceback (the edits of the alignment, Sec. 1) follows, from the
+//       best cell back to the origin, the move that gave each cell its value,
+//       taking the diagonal first, then the step in a, then the step in b
+//       when values are equal; the seeded alignment's columns are the left
+//       extension's reversed, the seed's, then the right extension's, in A
+//       and B' (B reverse complemented for strand 1).
 // Arithmetic is int64 (the paper fixes no precision; scores are integers).
 //
 // Parity pinned by the tests: hand-worked examples (golden files), an
 // independent full dynamic program for X = infinity, brute-force enumeration
 // of all alignments on tiny inputs, and invariants (mirror symmetry, X
-// monotonicity bound, cell bounds).
+// monotonicity bound, cell bounds); the traceback by hand-worked columns, by
+// an independent full-matrix traceback at X = infinity, and by rescoring the
+// columns against the sequences (they must consume exactly the aligned
+// ranges and add up to the reported score).
 
 #include <algorithm>
 #include <atomic>
@@ -71,9 +80,21 @@ struct Antidiagonal {
 
 // One-direction X-drop extension of a[0..m) against b[0..n), starting from
 // the cell (0,0) that holds score 0.  i indexes a, j indexes b, d = i + j.
+// Predecessor of an evaluated cell, for the traceback: the move that gave its
+// value, taking on equal values the diagonal first, then the step in a, then
+// the step in b (kFromNone: no live predecessor, the cell is dead).
+enum : uint8_t { kFromNone = 0, kFromDiag = 1, kFromUp = 2, kFromLeft = 3 };
+
+// Predecessors of every evaluated cell: moves[d] holds antidiagonal d's band
+// [move_lo[d], move_lo[d] + moves[d].size()).
+struct Moves {
+  std::vector<std::vector<uint8_t>> moves;
+  std::vector<int64_t> move_lo;
+};
+
 ExtOut extend(const char* a, int64_t m, const char* b, int64_t n, int64_t match,
               int64_t mismatch, int64_t gap, int64_t xdrop,
-              std::vector<int64_t>* band_sizes = nullptr) {
+              std::vector<int64_t>* band_sizes = nullptr, Moves* record = nullptr) {
   ExtOut out{0, 0, 0, 0, 0};
   Antidiagonal d2, d1, d0;  // antidiagonals d-2, d-1, d
   d2.h.assign((size_t)m + 1, kNegInf);
@@ -86,6 +107,10 @@ ExtOut extend(const char* a, int64_t m, const char* b, int64_t n, int64_t match,
   d1.h[0] = 0;
   int64_t live_lo = 0, live_hi = 0;  // live cells of antidiagonal d-1
   int64_t best = 0;
+  if (record) {  // antidiagonal 0: the origin, reached by no move
+    record->moves.assign(1, std::vector<uint8_t>(1, kFromNone));
+    record->move_lo.assign(1, 0);
+  }
 
   for (int64_t d = 1; d <= m + n; ++d) {
     // R1: band of d from the live cells of d-1, clipped to 0<=i<=m, 0<=j<=n.
@@ -95,32 +120,49 @@ ExtOut extend(const char* a, int64_t m, const char* b, int64_t n, int64_t match,
     d0.lo = lo;
     d0.hi = hi;
     const int64_t threshold = best - xdrop;  // R2: fixed for this antidiagonal
+    if (record) {
+      record->moves.emplace_back((size_t)(hi - lo + 1), kFromNone);
+      record->move_lo.push_back(lo);
+    }
 
     int64_t row_best = kNegInf, row_best_i = -1, row_best_count = 0;
     int64_t new_live_lo = -1, new_live_hi = -1;
     for (int64_t i = lo; i <= hi; ++i) {
       const int64_t j = d - i;
       int64_t h = kNegInf;
+      uint8_t from = kFromNone;
       // H(i-1, j-1) + s(a[i-1], b[j-1]): antidiagonal d-2, index i-1.
       if (i >= 1 && j >= 1) {
         const int64_t diag = d2.at(i - 1);
-        if (diag != kNegInf)
-          h = std::max(h, diag + substitution(a[i - 1], b[j - 1], match, mismatch));
+        if (diag != kNegInf) {
+          const int64_t v = diag + substitution(a[i - 1], b[j - 1], match, mismatch);
+          if (v > h) {
+            h = v;
+            from = kFromDiag;
+          }
+        }
       }
       // H(i-1, j) + gap: antidiagonal d-1, index i-1.
       if (i >= 1) {
         const int64_t up = d1.at(i - 1);
-        if (up != kNegInf) h = std::max(h, up + gap);
+        if (up != kNegInf && up + gap > h) {
+          h = up + gap;
+          from = kFromUp;
+        }
       }
       // H(i, j-1) + gap: antidiagonal d-1, index i.
       if (j >= 1) {
         const int64_t left = d1.at(i);
-        if (left != kNegInf) h = std::max(h, left + gap);
+        if (left != kNegInf && left + gap > h) {
+          h = left + gap;
+          from = kFromLeft;
+        }
       }
       out.cells += 1;  // R4: every cell of the band is evaluated
       const bool live = (h != kNegInf) && (h >= threshold);  // R2
       d0.h[(size_t)i] = live ? h : kNegInf;
       if (!live) continue;
+      if (record) record->moves.back()[(size_t)(i - lo)] = from;
       if (new_live_lo < 0) new_live_lo = i;
       new_live_hi = i;
       if (h > row_best) {  // ascending i: first maximum = smallest i
@@ -148,6 +190,43 @@ ExtOut extend(const char* a, int64_t m, const char* b, int64_t n, int64_t match,
     std::swap(d1, d0);
   }
   return out;
+}
+
+// The edits of the best extension (Sec. 1: an alignment is the list of edits
+// that makes the two overlapping regions identical; Sec. 2: its columns pair
+// two characters or a character with a gap).  Walks the recorded moves back
+// from the best cell to the origin and returns the columns from the origin
+// on: '=' equal pair, 'X' unequal pair, 'D' a character of a against a gap,
+// 'I' a character of b against a gap.  Returns false if a cell on the way has
+// no move (cannot happen for a cell the extension reported).
+bool trace_columns(const char* a, const char* b, int64_t i, int64_t j, const Moves& mv,
+                   std::string* cols) {
+  std::string rev;
+  while (i > 0 || j > 0) {
+    const int64_t d = i + j;
+    if (d >= (int64_t)mv.moves.size()) return false;
+    const int64_t at = i - mv.move_lo[(size_t)d];
+    if (at < 0 || at >= (int64_t)mv.moves[(size_t)d].size()) return false;
+    switch (mv.moves[(size_t)d][(size_t)at]) {
+      case kFromDiag:
+        rev.push_back(a[i - 1] == b[j - 1] ? '=' : 'X');
+        --i;
+        --j;
+        break;
+      case kFromUp:
+        rev.push_back('D');
+        --i;
+        break;
+      case kFromLeft:
+        rev.push_back('I');
+        --j;
+        break;
+      default:
+        return false;
+    }
+  }
+  cols->assign(rev.rbegin(), rev.rend());
+  return true;
 }
 
 char complement(char c) {
@@ -246,6 +325,54 @@ OracleResult align_seed(const std::string& A, const std::string& B, const Oracle
   r.status = seed_exact ? 0 : kStatusSeedMismatch;
   r.cells = L.cells + R.cells;
   return r;
+}
+
+// Columns of the whole seeded alignment, from (begin_a, begin_b') to
+// (end_a, end_b') in A and B' (B reverse complemented when strand = 1): the
+// left extension's columns in reverse order (it ran on reversed prefixes), the
+// k seed columns, then the right extension's columns.  Empty for an invalid
+// seed; false if a traceback failed.
+bool seed_columns(const std::string& A, const std::string& B, const OraclePair& p, int64_t k,
+                  int64_t match, int64_t mismatch, int64_t gap, int64_t xdrop,
+                  OracleResult* res, std::string* cols) {
+  cols->clear();
+  *res = align_seed(A, B, p, k, match, mismatch, gap, xdrop, nullptr, nullptr);
+  if (res->status & kStatusInvalidSeed) return true;
+  const int64_t len_b = (int64_t)B.size();
+  const std::string Bp = p.strand ? reverse_complement(B) : B;
+  const int64_t pa = p.pos_a;
+  const int64_t pb = p.strand ? len_b - (int64_t)p.pos_b - k : (int64_t)p.pos_b;
+  const std::string la = reversed(A.substr(0, (size_t)pa));
+  const std::string lb = reversed(Bp.substr(0, (size_t)pb));
+  const std::string ra = A.substr((size_t)(pa + k));
+  const std::string rb = Bp.substr((size_t)(pb + k));
+  Moves lm, rm;
+  const ExtOut L = extend(la.data(), (int64_t)la.size(), lb.data(), (int64_t)lb.size(), match,
+                          mismatch, gap, xdrop, nullptr, &lm);
+  const ExtOut R = extend(ra.data(), (int64_t)ra.size(), rb.data(), (int64_t)rb.size(), match,
+                          mismatch, gap, xdrop, nullptr, &rm);
+  std::string lc, rc;
+  if (!trace_columns(la.data(), lb.data(), L.i_end, L.j_end, lm, &lc)) return false;
+  if (!trace_columns(ra.data(), rb.data(), R.i_end, R.j_end, rm, &rc)) return false;
+  cols->assign(lc.rbegin(), lc.rend());
+  for (int64_t t = 0; t < k; ++t) cols->push_back(A[(size_t)(pa + t)] == Bp[(size_t)(pb + t)] ? '=' : 'X');
+  cols->append(rc);
+  return true;
+}
+
+// Run-length encoding of columns as 32-bit words (run length << 4 | op), with
+// the SAM/BAM op numbers: 7 '=', 8 'X', 1 'I', 2 'D'.
+std::vector<uint32_t> run_length(const std::string& cols) {
+  std::vector<uint32_t> out;
+  size_t t = 0;
+  while (t < cols.size()) {
+    size_t u = t;
+    while (u < cols.size() && cols[u] == cols[t]) ++u;
+    const uint32_t op = cols[t] == '=' ? 7u : cols[t] == 'X' ? 8u : cols[t] == 'I' ? 1u : 2u;
+    out.push_back(((uint32_t)(u - t) << 4) | op);
+    t = u;
+  }
+  return out;
 }
 
 // Per candidate pair (a run of consecutive records with equal read ids), flag
@@ -356,6 +483,56 @@ int oracle_xdrop_batch(const char* ascii, const int64_t* offsets, int64_t n_read
     for (auto& th : pool) th.join();
   }
   flag_best_of_pair(pairs, results, n_pairs);
+  return 0;
+}
+
+// Columns of one extension's best alignment as characters ('=', 'X', 'D',
+// 'I'; see trace_columns).  Returns their number (at most `cap` are written),
+// or -1 if the traceback failed.
+int64_t oracle_extend_columns(const char* a, int64_t m, const char* b, int64_t n, int32_t match,
+                              int32_t mismatch, int32_t gap, int32_t xdrop, char* cols,
+                              int64_t cap) {
+  Moves mv;
+  const ExtOut e = extend(a, m, b, n, match, mismatch, gap, xdrop, nullptr, &mv);
+  std::string c;
+  if (!trace_columns(a, b, e.i_end, e.j_end, mv, &c)) return -1;
+  for (int64_t t = 0; t < (int64_t)c.size() && t < cap; ++t) cols[t] = c[(size_t)t];
+  return (int64_t)c.size();
+}
+
+// A batch of seeds with the traceback of each: results as oracle_xdrop_batch
+// (without the best-of-pair flag) and, per seed t, its run-length encoded
+// columns in ops[t * cap_per_seed ...] with n_ops[t] runs; n_ops[t] = -1 when
+// more than cap_per_seed runs were needed (nothing written), 0 for an invalid
+// seed.  Single-threaded.  Returns 0, -1 on a bad argument, -2 if a traceback
+// failed.
+int oracle_traceback_batch(const char* ascii, const int64_t* offsets, int64_t n_reads,
+                           const void* pairs_v, int64_t n_pairs, int32_t k, int32_t match,
+                           int32_t mismatch, int32_t gap, int32_t xdrop, void* results_v,
+                           uint32_t* ops, int64_t cap_per_seed, int32_t* n_ops) {
+  if (n_pairs < 0 || n_reads < 0 || k < 1 || cap_per_seed < 0) return -1;
+  const OraclePair* pairs = static_cast<const OraclePair*>(pairs_v);
+  OracleResult* results = static_cast<OracleResult*>(results_v);
+  for (int64_t t = 0; t < n_pairs; ++t) {
+    const OraclePair& p = pairs[t];
+    n_ops[t] = 0;
+    if ((int64_t)p.read_a >= n_reads || (int64_t)p.read_b >= n_reads) {
+      std::memset(&results[t], 0, sizeof(OracleResult));
+      results[t].status = kStatusInvalidSeed;
+      continue;
+    }
+    const std::string A(ascii + offsets[p.read_a], (size_t)(offsets[p.read_a + 1] - offsets[p.read_a]));
+    const std::string B(ascii + offsets[p.read_b], (size_t)(offsets[p.read_b + 1] - offsets[p.read_b]));
+    std::string cols;
+    if (!seed_columns(A, B, p, k, match, mismatch, gap, xdrop, &results[t], &cols)) return -2;
+    const std::vector<uint32_t> runs = run_length(cols);
+    if ((int64_t)runs.size() > cap_per_seed) {
+      n_ops[t] = -1;
+      continue;
+    }
+    for (size_t r = 0; r < runs.size(); ++r) ops[t * cap_per_seed + (int64_t)r] = runs[r];
+    n_ops[t] = (int32_t)runs.size();
+  }
   return 0;
 }
 
