@@ -321,6 +321,56 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
                             dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
                             void* workspace, int64_t workspace_bytes, void* stream);
 
+/* ---- traceback ---------------------------------------------------------- */
+/* The edits of each seed's best alignment (Sec. 1: an alignment is the list
+ * of edits that makes two overlapping regions identical; Sec. 2: the columns
+ * of an alignment pair two characters or a character with a gap).  Each seed
+ * is aligned as by dibella_xdrop_batch (same band, prune and tie rules) while
+ * every evaluated cell keeps the move that gave its value, the diagonal
+ * first, then the step in A, then the step in B' on equal values; the walk
+ * from each extension's best cell back to the seed follows those moves.
+ * Columns run from (begin_a, begin_b') to (end_a, end_b') in A and B' (B
+ * reverse complemented when strand = 1): the left extension's, the k seed
+ * columns, the right extension's.  They are written run-length encoded, one
+ * 32-bit word per run: run length << 4 | op, with the SAM/BAM op numbers
+ * below ('I' = a base of B' against a gap, 'D' = a base of A against a gap). */
+#define DIBELLA_OP_INS 1
+#define DIBELLA_OP_DEL 2
+#define DIBELLA_OP_EQ 7
+#define DIBELLA_OP_DIFF 8
+
+/* Workspace for dibella_xdrop_traceback: n_lanes slots of
+ * 3 x (max_read_len + 2) int32 (H rows) + moves_words 32-bit words (the moves
+ * of every evaluated antidiagonal up to the best one: 3 words per
+ * antidiagonal plus 2 bits per cell), rounded up to 256 bytes.  EINVAL for
+ * n_lanes outside 1..2^24, moves_words outside 2..2^34, max_read_len outside
+ * 0..DIBELLA_MAX_READ_LEN. */
+int dibella_traceback_workspace_bytes(int64_t n_lanes, int32_t max_read_len, int64_t moves_words,
+                                      int64_t* bytes_out);
+
+/* DEVICE pointers: the store (as for dibella_xdrop_batch; no read longer than
+ * max_read_len), pairs (n_pairs records), results (n_pairs records, written
+ * as dibella_xdrop_batch writes them but without DIBELLA_RES_BEST_OF_PAIR),
+ * ops (n_pairs x ops_per_seed words: seed t's runs at t * ops_per_seed) and
+ * n_ops (n_pairs int32: seed t's run count; 0 for an invalid seed; -1 when
+ * more than ops_per_seed runs were needed, nothing claimed; -2 when an
+ * extension's moves up to its best cell exceeded moves_words; -3 when a read
+ * is longer than max_read_len, the result then carries
+ * DIBELLA_RES_BAND_OVERFLOW and zero fields).  Asynchronous on `stream`
+ * (a cudaStream_t); allocates nothing.  A thread per seed (n_lanes threads,
+ * each with one workspace slot) re-runs both extensions serially: a first
+ * form, meant for the seeds whose edits are wanted (accepted overlaps), not
+ * for whole candidate batches.  EINVAL on the scoring limits of
+ * dibella_xdrop_batch, k outside 1..32, ops_per_seed < 1, null or
+ * misaligned (256-byte) pointers or a size outside the limits above; ENOMEM
+ * when workspace_bytes is below dibella_traceback_workspace_bytes. */
+int dibella_xdrop_traceback(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                            const int32_t* read_lengths, int64_t n_reads, int32_t max_read_len,
+                            const dibella_pair_t* pairs, int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
+                            dibella_result_t* results, uint32_t* ops, int32_t ops_per_seed, int32_t* n_ops,
+                            int64_t n_lanes, int64_t moves_words, void* workspace, int64_t workspace_bytes,
+                            void* stream);
+
 /* ---- autotuning -------------------------------------------------------- */
 /* Pick a schedule for batches like this one: runs dibella_xdrop_batch on the
  * given (sample) batch with candidate schedules and returns the fastest in

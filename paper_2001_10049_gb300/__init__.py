@@ -118,6 +118,9 @@ def _lib():
             "dibella_candidate_workspace_bytes": ([i64, i64, i32, i32, p64], i32),
             "dibella_candidate_pairs": ([vp, vp, vp, i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64,
                                          vp], i32),
+            "dibella_traceback_workspace_bytes": ([i64, i32, i64, p64], i32),
+            "dibella_xdrop_traceback": ([vp, vp, vp, i64, i32, vp, i64, i32, Scoring, vp, vp, i32, vp, i64, i64,
+                                         vp, i64, vp], i32),
             "dibella_last_error": ([], ctypes.c_char_p),
             "dibella_version": ([], ctypes.c_char_p),
         }
@@ -222,6 +225,32 @@ def dibella_candidate_pairs(words, word_offsets, lengths, n_reads: int, n_bases:
                                           max_read_len, k, mult_lo, mult_hi, max_seeds, min_seed_gap,
                                           _ptr(pairs_out), pairs_capacity, _ptr(counts_out), _ptr(workspace),
                                           workspace_bytes, _stream_handle(stream)), "dibella_candidate_pairs")
+
+
+def dibella_traceback_workspace_bytes(n_lanes: int, max_read_len: int, moves_words: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_traceback_workspace_bytes(n_lanes, max_read_len, moves_words, ctypes.byref(out)),
+           "dibella_traceback_workspace_bytes")
+    return out.value
+
+
+def dibella_xdrop_traceback(packed_words, read_word_offsets, read_lengths, n_reads: int, max_read_len: int, pairs,
+                            n_pairs: int, k: int, scoring: Scoring, results, ops, ops_per_seed: int, n_ops,
+                            n_lanes: int, moves_words: int, workspace, workspace_bytes: int, stream=None) -> None:
+    _check(_lib().dibella_xdrop_traceback(_ptr(packed_words), _ptr(read_word_offsets), _ptr(read_lengths), n_reads,
+                                          max_read_len, _ptr(pairs), n_pairs, k, scoring, _ptr(results),
+                                          _ptr(ops), ops_per_seed, _ptr(n_ops), n_lanes, moves_words,
+                                          _ptr(workspace), workspace_bytes, _stream_handle(stream)),
+           "dibella_xdrop_traceback")
+
+
+# Op letters of the run-length encoded traceback words (run << 4 | op).
+CIGAR_LETTERS = {1: "I", 2: "D", 7: "=", 8: "X"}
+
+
+def cigar_string(words) -> str:
+    """Text form of one seed's run words, e.g. '120=1X40=1I8='."""
+    return "".join("%d%s" % (int(w) >> 4, CIGAR_LETTERS[int(w) & 15]) for w in words)
 
 
 def dibella_staging_bytes(n_pairs: int) -> int:

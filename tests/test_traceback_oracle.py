@@ -170,3 +170,29 @@ def test_seed_batch_columns_rescore_and_match_the_batch():
     # too small a capacity: -1, nothing claimed
     _, _, few = oracle.traceback_batch(ascii, offs, pairs, k, M, S, G, X, 1)
     assert all(v == -1 or v == n for v, n in zip(few, n_ops)) and (few == -1).any()
+
+
+def test_gpu_traceback_entry_points_validate_arguments_on_the_host():
+    import paper_2001_10049_gb300 as dib
+    assert dib.dibella_traceback_workspace_bytes(4, 100, 64) == 4 * 1536  # 3 x 102 x 4 + 64 x 4, to 256 B
+    for bad in ((0, 100, 64), (4, -1, 64), (4, 100, 1), (4, (1 << 24) + 1, 64), ((1 << 24) + 1, 100, 64)):
+        with pytest.raises(dib.DibellaError):
+            dib.dibella_traceback_workspace_bytes(*bad)
+    ws = 1 << 20  # a fake, aligned device address: every call below fails before touching it
+    sc = dib.Scoring(1, -1, -1, 7)
+    good = dict(n_reads=2, max_len=100, n_pairs=3, k=17, sc=sc, ops_per_seed=8, lanes=4, moves=64, ws_bytes=1 << 30)
+    cases = [dict(good, k=0), dict(good, k=33), dict(good, sc=dib.Scoring(0, -1, -1, 7)),
+             dict(good, sc=dib.Scoring(1, 1, -1, 7)), dict(good, sc=dib.Scoring(1, -1, 0, 7)),
+             dict(good, sc=dib.Scoring(1, -1, -1, -1)), dict(good, ops_per_seed=0), dict(good, lanes=0),
+             dict(good, moves=1), dict(good, n_pairs=-1), dict(good, max_len=-1)]
+    for c in cases:
+        with pytest.raises(dib.DibellaError) as e:
+            dib.dibella_xdrop_traceback(ws, ws, ws, c["n_reads"], c["max_len"], ws, c["n_pairs"], c["k"], c["sc"], ws,
+                                        ws, c["ops_per_seed"], ws, c["lanes"], c["moves"], ws, c["ws_bytes"], stream=0)
+        assert e.value.code == dib.DIBELLA_EINVAL
+    with pytest.raises(dib.DibellaError) as e:  # a misaligned workspace
+        dib.dibella_xdrop_traceback(ws, ws, ws, 2, 100, ws, 3, 17, sc, ws, ws, 8, ws, 4, 64, ws + 16, 1 << 30, stream=0)
+    assert e.value.code == dib.DIBELLA_EINVAL
+    with pytest.raises(dib.DibellaError) as e:  # too small a workspace
+        dib.dibella_xdrop_traceback(ws, ws, ws, 2, 100, ws, 3, 17, sc, ws, ws, 8, ws, 4, 64, ws, 6143, stream=0)
+    assert e.value.code == dib.DIBELLA_ENOMEM
