@@ -36,8 +36,23 @@ WORKLOAD = "c2_ecoli"
 XDROPS = (7, 25)
 K = 17
 OPS_PER_CELL = 8      # integer ops per DP cell (3 diagonal, 2 gap, 1 max, 2 prune)
-SM_COUNT = 152
-INT32_LANES_PER_SM = 128
+INT32_LANES_PER_SM = 128   # nominal INT32 lanes per SM (the unit-count peak); the SM count is queried
+
+
+def measured_int_peaks(dib, stream, clock_gpu):
+    """Lane-ops/s of each integer class the extension kernels issue, from the
+    library's microbenchmark (a full grid of independent chains per class), with
+    the median SM clock sampled while it ran."""
+    out = {}
+    with ClockSampler(clock_gpu) as clk:
+        for c, name in dib.INT_PEAK_CLASSES.items():
+            iters = 1 << 16
+            ops, ms = dib.dibella_int_peak(c, iters, stream=stream)
+            if ms < 40.0:  # long enough to dwarf launch overhead
+                iters = int(iters * 60.0 / max(ms, 0.01))
+                ops, ms = dib.dibella_int_peak(c, iters, stream=stream)
+            out[name] = {"class": c, "tops": ops / 1e12, "ms": round(ms, 2)}
+    return out, clk.summary()
 
 
 def parse():
@@ -63,6 +78,12 @@ def parse():
                          "serve: continuous-batching request loop at three offered loads; candidates: GPU "
                          "candidate-pair generation (k-mer counting to seeds) on the E. coli-sized reads")
     ap.add_argument("--chunk-pairs", type=int, default=4_000_000)
+    ap.add_argument("--stream-workload", default="c4_repeats",
+                    help="stream mode: c4_repeats (the configured 100 Mb genome, candidate pairs from the GPU) "
+                         "or c4_repeats_small (1/20 genome, pairs from the generator's index)")
+    ap.add_argument("--stream-genome", type=int, default=0,
+                    help="stream mode: override the genome length (repeat content scaled with it)")
+    ap.add_argument("--n-parts", type=int, default=8, help="stream mode: hash passes of the k-mer count")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     args = ap.parse_args()
@@ -311,7 +332,7 @@ def mode_tune(args):
         tune_s = time.perf_counter() - t0
         tuned_ms = _time_direct(torch, al, n, sc, stream, best, args.steps)
     c_tuned = dib.dibella_batch_counters(al.workspace, stream=stream)
-    cells = sum(c_tuned[c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global"))
+    cells = sum(c_tuned[c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_mid"))
     n_cand = len(workloads.pair_groups(pairs)) - 1
     cpu = None if args.no_cpu else cpu_baseline(w, args.cpu_seconds, (X,))
     print(json.dumps({
@@ -329,6 +350,101 @@ def mode_tune(args):
                               "%d seed records" % (len(workloads.pair_groups(tw.pairs)) - 1, len(tw.pairs))},
         "speedup_tuned_vs_fixed": fixed_ms / tuned_ms,
         "clocks": clocks.summary(),
+    }))
+
+
+def mode_stream_full(args):
+    """The repeat-rich configuration at its stated size: a 100 Mb genome with
+    200 families x 2 copies of 5 kb repeats (3% divergence) and 1 Mb of tandem
+    arrays, reads at 40x (lognormal 9 kb +- 7 kb, 15% error).  The generator
+    gives the reads only; the GPU counts the k-mers in hash-partitioned passes
+    (k = 17, multiplicity [2, 12]) and writes every candidate pair's seed; the
+    records go to host memory and come back through dibella_xdrop_stream in
+    chunks of 4M records (X = 15), the read store resident in HBM.  value =
+    candidate pairs / wall clock of the streamed alignment (host copies into
+    pinned windows, H2D, kernels, D2H); e2e adds the candidate generation and
+    the copy of its records to the host."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    from paper_2001_10049_gb300.streaming import align_all_candidates
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X = 15
+    over = {}
+    if args.stream_genome:
+        scale = args.stream_genome / 100_000_000
+        over = dict(genome_len=args.stream_genome, repeat_families=max(1, int(round(200 * scale))),
+                    tandem_bases=int(1_000_000 * scale))
+    t0 = time.perf_counter()
+    w = workloads.generate("c4_repeats", pairs_mode=workloads.PAIRS_NONE, cache=False, **over)
+    t_gen = time.perf_counter() - t0
+    # CPU baseline inputs: the generator's own index restricted to a few read
+    # ranges (never the GPU's records), built on the host while the GPU works.
+    n = w.n_reads
+    sample_ranges = [(0, 40), (n // 2, n // 2 + 40), (n - 80, n - 40)]
+    base_in = {}
+
+    def index_sample():
+        base_in["w"] = workloads.generate("c4_repeats", pairs_mode=workloads.PAIRS_RANGES,
+                                          read_ranges=sample_ranges, cache=False, **over)
+
+    th = threading.Thread(target=index_sample)
+    if not args.no_cpu:
+        th.start()
+    t0 = time.perf_counter()
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    t_pack = time.perf_counter() - t0
+    n_bases = int(len(w.reads))
+    del w
+    log = []
+    with ClockSampler(0) as clocks:
+        out = align_all_candidates(store, dib.Scoring(1, -1, -1, X), k=K, mult_lo=2, mult_hi=12, max_seeds=1,
+                                   n_parts=args.n_parts, chunk_pairs=args.chunk_pairs,
+                                   log=lambda m: log.append((round(time.perf_counter(), 1), m)))
+    if not args.no_cpu:
+        th.join()
+    cand = out["candidates"]
+    dt = out["t_stream"]
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sm_count * INT32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    int_peaks, int_clk = measured_int_peaks(dib, torch.cuda.current_stream(dev), 0)
+    cell_peak = int_peaks[dib.INT_PEAK_CLASSES[4]]["tops"]
+    achieved = OPS_PER_CELL * out["cells"] / dt / 1e12
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(base_in["w"], args.cpu_seconds, (X,))
+        cpu["sample"] += "; records from the generator's index restricted to read_a in %s" % sample_ranges
+    e2e_s = out["t_candidates"] + out["t_to_host"] + dt
+    print(json.dumps({
+        "metric": "aligned pairs/s", "mode": "stream", "value": cand["candidate_pairs"] / dt,
+        "unit": "aligned pairs/s", "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "gcups": out["cells"] / dt / 1e9, "cpu_baseline": cpu,
+        "e2e": {"value": cand["candidate_pairs"] / e2e_s, "unit": "aligned pairs/s",
+                "includes": "GPU candidate generation + records to host + streamed alignment",
+                "h2d_bytes_per_step": out["records"] * 24, "d2h_bytes_per_step": out["records"] * 64},
+        "config": {"workload": "c4_repeats" + (" (genome %d bp)" % args.stream_genome if over else ""),
+                   "genome_bp": over.get("genome_len", 100_000_000), "coverage": 40, "reads": int(n),
+                   "bases": n_bases, "candidate_pairs": cand["candidate_pairs"], "seed_records": out["records"],
+                   "kmer_occurrences": cand["instances"], "retained_kmers": cand["retained_kmers"],
+                   "occurrence_pairs": cand["occurrence_pairs"], "largest_pass_occurrences": cand["max_pass"],
+                   "n_parts": args.n_parts, "chunk_pairs": out["chunk_pairs"], "chunks": out["chunks"],
+                   "window_pairs": out["window_pairs"], "xdrop": X, "k": K, "multiplicity": [2, 12],
+                   "store_bytes_hbm": store.nbytes,
+                   "timing": "wall clock of the streamed alignment of every seed record, incl. host copies"},
+        "seconds": {"generate_reads": round(t_gen, 1), "pack_and_upload": round(t_pack, 1),
+                    "gpu_candidates": round(out["t_candidates"], 2), "records_to_host": round(out["t_to_host"], 2),
+                    "stream": round(dt, 1)},
+        "cells": out["cells"], "status_counts": {str(k): v for k, v in sorted(out["status"].items())},
+        "best_of_pair_flags": out["best_of_pair"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "whole streamed batch (all extension launches), %d cells" % out["cells"],
+                     "peak_source": "%d SMs x %d INT32 lanes x %.0f MHz (%s sm_max_mhz)"
+                                    % (sm_count, INT32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), pk_kind),
+                     "peak_measured": cell_peak, "frac_measured": achieved / cell_peak,
+                     "int_peaks_clocks": int_clk},
+        "clocks": clocks.summary(), "progress": log[-3:],
     }))
 
 
@@ -555,7 +671,9 @@ def main():
         return
     if args.mode != "batch":
         if rank == 0:
-            {"tune": mode_tune, "stream": mode_stream, "serve": mode_serve,
+            {"tune": mode_tune,
+             "stream": mode_stream if args.stream_workload == "c4_repeats_small" else mode_stream_full,
+             "serve": mode_serve,
              "candidates": mode_candidates}[args.mode](args)
         return
     import torch
@@ -598,7 +716,8 @@ def main():
                 al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
             graphs[X] = g
     torch.cuda.synchronize(dev)
-    cells = {X: sum(counters[X][c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global"))
+    cells = {X: sum(counters[X][c] for c in ("cells_narrow", "cells_wide", "cells_smem", "cells_global",
+                                             "cells_mid"))
              for X in XD}
 
     def one_step(record):
@@ -682,14 +801,15 @@ def main():
     # Roofline of the dominant kernel: integer ops of the cells its launch
     # finished / that launch's duration, from the phase events recorded on the
     # launching stream inside every replayed graph of the timed region.
-    # phases: 0 queueing, 1 narrow form, 2 first wide launch, 3 wide launch on
-    # the narrow escalations, 4 slot ladder + CTA + global forms, 5 combine
-    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 6]), axis=0) for X in XD}
+    # phases: 0 queueing, 1 narrow form, 2 first wide launch, 3 mid form, 4 wide
+    # launch on the escalations, 5 slot ladder + CTA + global forms, 6 combine
+    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 7]), axis=0) for X in XD}
     batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XD}
     launch_cells = {X: {"narrow form": (1, counters[X]["cells_narrow"]),
                         "wide form, first launch": (2, counters[X]["cells_wide"] - counters[X]["cells_wide_esc"]
                                                      - counters[X]["cells_ladder"]),
-                        "wide form on the narrow escalations": (3, counters[X]["cells_wide_esc"])}
+                        "mid form on the narrow escalations": (3, counters[X]["cells_mid"]),
+                        "wide form on the escalations": (4, counters[X]["cells_wide_esc"])}
                     for X in XD}
     per_launch = {X: {name: {"ms": float(phase[X][i]), "cells": int(c),
                              "tops": OPS_PER_CELL * c / (phase[X][i] * 1e-3) / 1e12 if phase[X][i] > 0 else 0.0}
@@ -699,7 +819,10 @@ def main():
     dom_rec = per_launch[domX][domName]
     dom = {X: max(per_launch[X], key=lambda nm: per_launch[X][nm]["ms"]) for X in XD}
     achieved = dom_rec["tops"]
-    peak_ops = SM_COUNT * INT32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sm_count * INT32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    int_peaks, int_clk = measured_int_peaks(dib, stream, local)
+    cell_peak = int_peaks[dib.INT_PEAK_CLASSES[4]]["tops"]
     total_cells = sum(cells.values())
     value = world * len(XD) * n_cand / (my_ms * 1e-3)
     out = {
@@ -736,8 +859,12 @@ def main():
                      "kernel": "%s (X=%d), %d cells in %.1f ms per launch" % (domName, domX, dom_rec["cells"],
                                                                             dom_rec["ms"]),
                      "peak_source": "%d SMs x %d INT32 lanes x %.0f MHz (%s sm_max_mhz)"
-                                    % (SM_COUNT, INT32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), pk_kind),
-                     "ops_per_cell": OPS_PER_CELL},
+                                    % (sm_count, INT32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), pk_kind),
+                     "ops_per_cell": OPS_PER_CELL,
+                     "peak_measured": cell_peak, "frac_measured": achieved / cell_peak,
+                     "peak_measured_class": "int32 DP cell, 8 ops (compare, select, add; max, add; max; "
+                                            "compare, select), full grid of independent chains",
+                     "int_peaks_measured": int_peaks, "int_peaks_clocks": int_clk},
         "e2e": ({"value": world * len(XD) * n_cand / (e2e_step * 1e-3), "unit": "aligned pairs/s",
                  "h2d_bytes_per_step": len(XD) * n_seeds * 24, "d2h_bytes_per_step": len(XD) * n_seeds * 40}
                 if e2e_step else None),

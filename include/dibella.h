@@ -126,8 +126,12 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  *           packed as int16 pairs when wide_packed is set and
  *           xdrop <= 8000 (exact: scores are kept relative to a moving base),
  *           else 32 int32 cells of one warp;
+ *   mid     the narrow form's escalations first go, when mid_band_cap > 0
+ *           and xdrop <= 8000, to a second one-thread-per-extension form
+ *           whose per-thread band holds mid_band_cap int16 cells (one warp
+ *           per block); its own escalations go to the wide form;
  * an extension whose band outgrows its form is re-run from the start by the
- * next wider form: the narrow form's by the wide form, the wide form's by
+ * next wider form: the narrow form's by the mid (else the wide) form, the wide form's by
  * the next rung of 8 -> 16 -> 24 -> 32 slots, then by a block of 8 warps
  * per extension with an 8192-cell band in shared memory (the CTA form), and
  * beyond that by a warp whose band lives in the workspace (sized by
@@ -158,6 +162,7 @@ typedef struct {
   int32_t narrow_blocks_per_sm;   /* 0 = occupancy maximum                   */
   int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
   int32_t bucket_bounds[DIBELLA_MAX_BUCKETS];
+  int32_t mid_band_cap;           /* mid form: 0 (none), 128, 192 or 256      */
 } dibella_schedule_t;
 
 /* The schedule used when a call passes NULL.  set() validates (EINVAL). */
@@ -215,15 +220,21 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
  * that may not hold allocations of its own.  This entry point runs the same
  * alignment as dibella_xdrop_batch (same arguments, results and semantics,
  * default schedule) without any workspace from the caller and without
- * allocating.  Its scratch is one fixed array inside the library, 9,306,624
- * bytes (about 8.9 MiB), which every GPU that loads the library keeps until
+ * allocating.  Its scratch is one fixed array inside the library, 9,437,696
+ * bytes (about 9.0 MiB), which every GPU that loads the library keeps until
  * the process exits.
  * Limits: at most DIBELLA_NOALLOC_MAX_PAIRS seed records per call (more
  * returns DIBELLA_ENOMEM, with the reason in dibella_last_error(), and does
- * nothing); an extension whose band outgrows the fixed scratch gets
- * DIBELLA_RES_BAND_OVERFLOW.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * nothing); an extension whose band (the cells of one antidiagonal between
+ * its first and last live cell, plus one) grows beyond
+ * DIBELLA_NOALLOC_MAX_BAND cells gets DIBELLA_RES_BAND_OVERFLOW and zero
+ * fields, where dibella_xdrop_batch with a workspace sized for the longest
+ * read computes it (such bands need X far above the read's error budget:
+ * about X >= 8000 with unit scores, or reads that agree over 8 kb or more at
+ * X = DIBELLA_XDROP_INF).
+ * Every call looks up the array's device address with cudaGetSymbolAddress
+ * (the first lookup on a device loads the library's module there), so make
+ * the first call on each device before any stream capture.
  * All calls share the one array and each leaves its contents behind; the
  * parts that must start at zero are cleared by every call, but calls whose
  * work overlaps on the GPU (other streams, other threads) race on it, so
@@ -231,6 +242,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
  * The paper has no counterpart: this is an interface for integration, not
  * part of the method. */
 #define DIBELLA_NOALLOC_MAX_PAIRS 16384
+#define DIBELLA_NOALLOC_MAX_BAND 8189
 int dibella_xdrop_batch_noalloc(const uint32_t* packed_words, const int64_t* read_word_offsets,
                                 const int32_t* read_lengths, int64_t n_reads, const dibella_pair_t* pairs,
                                 int64_t n_pairs, int32_t k, dibella_scoring_t scoring,
@@ -321,6 +333,44 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
                             dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
                             void* workspace, int64_t workspace_bytes, void* stream);
 
+/* The same candidate pairs for read sets too large for one sort key
+ * (dibella_candidate_pairs refuses more than 2^32 - 2 bases and occurrence-pair
+ * fields wider than 64 bits).  The k-mer count runs in n_parts passes, the
+ * paper's streaming of memory-limited phases (Sec. 4; Sec. 6-7 count the
+ * k-mers in passes bounded by memory): pass p takes every occurrence whose
+ * canonical code hashes to part p, so each k-mer is counted whole in one
+ * pass, and keys it by (code << b | slot) with b = bits of the pass capacity
+ * (n_bases / n_parts plus a quarter, plus 2^16 occurrences; 2k + b must not
+ * exceed 64, else EINVAL: for k = 17, at least n_bases / 2^29 parts).  The
+ * occurrence pairs of every pass (read_a, read_b, pos_a, pos_b, strand) are
+ * kept in occ_pair_capacity slots, one 64-bit key each, or two 64-bit words
+ * each (read_a | read_b, then pos_a | pos_b | strand) when the fields need
+ * more than 64 bits; then they are sorted and the seeds selected as above.
+ * Results are identical to dibella_candidate_pairs whenever both apply.
+ * Workspace bytes for n_bases bases in n_parts passes and occ_pair_capacity
+ * occurrence pairs (about 24 x 1.25 x n_bases / n_parts + 40 x
+ * occ_pair_capacity bytes with two-word keys).  EINVAL outside 1 <= k <= 32,
+ * 1 <= n_parts <= 4096, 0 <= occ_pair_capacity <= 2^40, 0 <= max_read_len <=
+ * DIBELLA_MAX_READ_LEN. */
+int dibella_candidate_workspace_bytes_parts(int64_t n_reads, int64_t n_bases, int32_t max_read_len, int32_t k,
+                                            int32_t n_parts, int64_t occ_pair_capacity, int64_t* bytes_out);
+
+/* Arguments as for dibella_candidate_pairs, plus n_parts and
+ * occ_pair_capacity as above (the workspace must be sized for them with the
+ * same n_reads, n_bases and max_read_len).  counts_out holds 7 int64: the six
+ * of dibella_candidate_pairs, then the occurrences of the largest pass; status
+ * bit 3 now means a pass held more occurrences than its capacity (use more
+ * parts), bit 1 more occurrence pairs than occ_pair_capacity.  Asynchronous on
+ * `stream`, allocates nothing.  Synchronous EINVAL on the argument limits of
+ * dibella_candidate_pairs (the 64-bit key limits excepted), n_reads > 2^32,
+ * or 2k + bits(pass capacity) > 64; ENOMEM when the workspace is too small. */
+int dibella_candidate_pairs_parts(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                                  const int32_t* read_lengths, int64_t n_reads, int64_t n_bases, int32_t max_read_len,
+                                  int32_t k, int32_t mult_lo, int32_t mult_hi, int32_t max_seeds,
+                                  int32_t min_seed_gap, int32_t n_parts, int64_t occ_pair_capacity,
+                                  dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
+                                  void* workspace, int64_t workspace_bytes, void* stream);
+
 /* ---- traceback ---------------------------------------------------------- */
 /* The edits of each seed's best alignment (Sec. 1: an alignment is the list
  * of edits that makes two overlapping regions identical; Sec. 2: the columns
@@ -376,7 +426,8 @@ int dibella_xdrop_traceback(const uint32_t* packed_words, const int64_t* read_wo
  * given (sample) batch with candidate schedules and returns the fastest in
  * *best_out (median of `repeats` timed runs each, CUDA events on `stream`).
  * The search is staged: routing threshold between the one-thread and the
- * wide forms x per-thread band chunk (32/48/64), then lanes per extension
+ * wide forms x per-thread band chunk (32/48/64), then the mid form's band
+ * (none/128/192/256), then lanes per extension
  * (32/16/8) x register slots (16/24/32) of the wide form, then resident
  * blocks per SM, then length-bucket bounds; each stage keeps the best so
  * far.  Same arguments as
@@ -393,14 +444,14 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
 
 /* ---- diagnostics ------------------------------------------------------ */
 /* Phase timing: when enabled, dibella_xdrop_batch records CUDA events on
- * `stream` at six points around its phases.  Under
+ * `stream` at eight points around its phases.  Under
  * stream capture they are recorded as external events, so a replayed CUDA
  * graph records them too.  dibella_phase_times() synchronises on the last
  * event and writes up to n_max phase durations in ms: queueing (expand, scan,
- * scatter), narrow form, first wide launch, the wide launch on the narrow
- * escalations, the slot ladder with the CTA and global forms, combine;
- * returns the count written (6 after a batch).  Enable it before any capture
- * (it creates the events). */
+ * scatter), narrow form, first wide launch, mid form (0 without one), the
+ * wide launch on the escalations, the slot ladder with the CTA and global
+ * forms, combine; returns the count written (7 after a batch).  Enable it
+ * before any capture (it creates the events). */
 int dibella_enable_phase_timing(int enable);
 int dibella_phase_times(float* ms_out, int n_max);
 
@@ -410,8 +461,10 @@ int dibella_phase_times(float* ms_out, int n_max);
  * overflows, out[6..9] evaluated cells of the extensions finished by the
  * narrow, wide (register or packed, all launches), CTA and global-band
  * forms, out[10] and out[11] the part of out[7] finished by the wide launch
- * on the narrow escalations and by the slot-ladder rungs.  Returns the
- * number written (<= n_max, at most 12), or a negative status. */
+ * on the escalations and by the slot-ladder rungs, out[12] the cells of the
+ * extensions finished by the mid form, out[13] extensions that outgrew the
+ * mid form.  Returns the number written (<= n_max, at most 14), or a
+ * negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 
 /* Number of kernels the calling thread's last dibella_xdrop_batch (or _host /
@@ -419,6 +472,21 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
  * queue is empty) and combine.  Host-side count; no device work, no errors.
  * The paper has no counterpart: it reports the GPU work of a batch. */
 int dibella_last_launch_count(void);
+
+/* Measured integer throughput of one instruction class, the ceiling the
+ * extension kernels' cell rates are compared with: every thread of a grid
+ * that fills each SM to its occupancy limit runs 8 independent chains of
+ * op_class for `iters` iterations (one untimed launch first, then one timed
+ * with CUDA events on `stream`).  Classes: 0 integer add (two dependent
+ * adds, 2 ops), 1 IMNMX (max then min, 2 ops), 2 int16x2 add-then-max (DPX,
+ * 2 instructions x 2 halves x 2 ops), 3 int16x2 three-way min and max (same
+ * count), 4 one int32 DP cell with the 8 ops of the cell convention
+ * (diagonal compare, select, add; gap max, add; final max; prune compare,
+ * select).  Writes lane-ops per second to *ops_per_s_out and the timed
+ * launch's duration to *ms_out (may be NULL).  Synchronous; EINVAL outside
+ * 0 <= op_class <= 4, 1 <= iters <= 2^30, or while `stream` is capturing.
+ * The paper has no counterpart: this is measurement infrastructure. */
+int dibella_int_peak(int32_t op_class, int64_t iters, double* ops_per_s_out, double* ms_out, void* stream);
 
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char* dibella_last_error(void);

@@ -28,6 +28,7 @@ RESULT_DTYPE = np.dtype(
 DIBELLA_OK, DIBELLA_EINVAL, DIBELLA_EBASE, DIBELLA_ENOMEM, DIBELLA_ECUDA, DIBELLA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 RES_SEED_MISMATCH, RES_INVALID_SEED, RES_BEST_OF_PAIR, RES_BAND_OVERFLOW = 1, 2, 4, 8
 XDROP_INF = 1 << 30
+DIBELLA_MAX_READ_LEN = 1 << 24
 MAX_BUCKETS = 8
 
 _ERRORS = {DIBELLA_EINVAL: "invalid argument", DIBELLA_EBASE: "non-ACGT base",
@@ -57,7 +58,7 @@ class Schedule(ctypes.Structure):
                 ("wide_packed", ctypes.c_int32), ("wide_group_lanes", ctypes.c_int32),
                 ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
-                ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS)]
+                ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS), ("mid_band_cap", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
@@ -65,7 +66,8 @@ class Schedule(ctypes.Structure):
                 "wide_packed": self.wide_packed, "wide_group_lanes": self.wide_group_lanes,
                 "wide_blocks_per_sm": self.wide_blocks_per_sm,
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
-                "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)]}
+                "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)],
+                "mid_band_cap": self.mid_band_cap}
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
@@ -74,6 +76,7 @@ class Schedule(ctypes.Structure):
                     "wide_group_lanes", "wide_blocks_per_sm",
                     "narrow_blocks_per_sm", "n_buckets"):
             setattr(s, key, int(d[key]))
+        s.mid_band_cap = int(d.get("mid_band_cap", 0))
         bounds = list(d.get("bucket_bounds", []))
         for b in range(MAX_BUCKETS):
             s.bucket_bounds[b] = int(bounds[b]) if b < len(bounds) else 0
@@ -115,9 +118,14 @@ def _lib():
             "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
             "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
             "dibella_last_launch_count": ([], i32),
+            "dibella_int_peak": ([i32, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp],
+                                 i32),
             "dibella_candidate_workspace_bytes": ([i64, i64, i32, i32, p64], i32),
             "dibella_candidate_pairs": ([vp, vp, vp, i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64,
                                          vp], i32),
+            "dibella_candidate_workspace_bytes_parts": ([i64, i64, i32, i32, i32, i64, p64], i32),
+            "dibella_candidate_pairs_parts": ([vp, vp, vp, i64, i64, i32, i32, i32, i32, i32, i32, i32, i64, vp, i64,
+                                               vp, vp, i64, vp], i32),
             "dibella_traceback_workspace_bytes": ([i64, i32, i64, p64], i32),
             "dibella_xdrop_traceback": ([vp, vp, vp, i64, i32, vp, i64, i32, Scoring, vp, vp, i32, vp, i64, i64,
                                          vp, i64, vp], i32),
@@ -227,6 +235,26 @@ def dibella_candidate_pairs(words, word_offsets, lengths, n_reads: int, n_bases:
                                           workspace_bytes, _stream_handle(stream)), "dibella_candidate_pairs")
 
 
+def dibella_candidate_workspace_bytes_parts(n_reads: int, n_bases: int, max_read_len: int, k: int, n_parts: int,
+                                            occ_pair_capacity: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib().dibella_candidate_workspace_bytes_parts(n_reads, n_bases, max_read_len, k, n_parts,
+                                                          occ_pair_capacity, ctypes.byref(out)),
+           "dibella_candidate_workspace_bytes_parts")
+    return out.value
+
+
+def dibella_candidate_pairs_parts(words, word_offsets, lengths, n_reads: int, n_bases: int, max_read_len: int,
+                                  k: int, mult_lo: int, mult_hi: int, max_seeds: int, min_seed_gap: int, n_parts: int,
+                                  occ_pair_capacity: int, pairs_out, pairs_capacity: int, counts_out, workspace,
+                                  workspace_bytes: int, stream=None) -> None:
+    _check(_lib().dibella_candidate_pairs_parts(_ptr(words), _ptr(word_offsets), _ptr(lengths), n_reads, n_bases,
+                                                max_read_len, k, mult_lo, mult_hi, max_seeds, min_seed_gap, n_parts,
+                                                occ_pair_capacity, _ptr(pairs_out), pairs_capacity, _ptr(counts_out),
+                                                _ptr(workspace), workspace_bytes, _stream_handle(stream)),
+           "dibella_candidate_pairs_parts")
+
+
 def dibella_traceback_workspace_bytes(n_lanes: int, max_read_len: int, moves_words: int) -> int:
     out = ctypes.c_int64(0)
     _check(_lib().dibella_traceback_workspace_bytes(n_lanes, max_read_len, moves_words, ctypes.byref(out)),
@@ -270,6 +298,7 @@ def dibella_xdrop_batch(packed_words, read_word_offsets, read_lengths, n_reads: 
 
 
 NOALLOC_MAX_PAIRS = 16384
+NOALLOC_MAX_BAND = 8189
 
 
 def dibella_xdrop_batch_noalloc(packed_words, read_word_offsets, read_lengths, n_reads: int, pairs,
@@ -345,13 +374,27 @@ def dibella_phase_times(n_max: int = 8) -> list[float]:
 
 
 def dibella_batch_counters(workspace, stream=None) -> dict:
-    buf = (ctypes.c_int64 * 12)()
-    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 12)
+    buf = (ctypes.c_int64 * 14)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 14)
     if n < 0:
         _check(n, "dibella_batch_counters")
     keys = ["narrow", "wide", "escalated_narrow", "escalated_wide", "escalated_smem", "band_overflow",
-            "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder"]
+            "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder",
+            "cells_mid", "escalated_mid"]
     return {keys[i]: int(buf[i]) for i in range(n)}
+
+
+INT_PEAK_CLASSES = {0: "IADD", 1: "IMNMX", 2: "VIADDMNMX int16x2", 3: "VIMNMX3 int16x2",
+                    4: "int32 DP cell (8 ops)"}
+
+
+def dibella_int_peak(op_class: int, iters: int, stream=None) -> tuple[float, float]:
+    """Measured lane-ops/s of one integer instruction class and the timed launch's ms."""
+    ops = ctypes.c_double(0)
+    ms = ctypes.c_double(0)
+    _check(_lib().dibella_int_peak(op_class, iters, ctypes.byref(ops), ctypes.byref(ms), _stream_handle(stream)),
+           "dibella_int_peak")
+    return float(ops.value), float(ms.value)
 
 
 def dibella_last_launch_count() -> int:

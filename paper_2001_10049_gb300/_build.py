@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdibella.so")
 SOURCES = [os.path.join(CSRC, "dibella_xdrop.cu"), os.path.join(CSRC, "dibella_kmers.cu"),
-           os.path.join(CSRC, "dibella_traceback.cu"), os.path.join(CSRC, "dibella_pack.cpp")]
+           os.path.join(CSRC, "dibella_traceback.cu"), os.path.join(CSRC, "dibella_peak.cu"),
+           os.path.join(CSRC, "dibella_pack.cpp")]
 HEADERS = [os.path.join(INCLUDE, "dibella.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()

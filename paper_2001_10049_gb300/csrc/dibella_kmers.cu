@@ -67,6 +67,9 @@ struct CandState {
   unsigned int status;            // bit 0 table full, bit 1 pair capacity, bit 2 output
                                   // capacity, bit 3 occurrence capacity, bit 4 sort inconsistency
   unsigned int pad;
+  unsigned long long pass_count;  // partitioned count: occurrences appended in this pass
+  unsigned long long pass_held;   // ... capped at the pass capacity
+  unsigned long long max_pass;    // ... the largest pass
 };
 
 // Warp-aggregated atomicAdd: every lane of the warp calls it (v = 0 allowed);
@@ -89,6 +92,56 @@ struct KeyLayout {  // bit positions of the packed occurrence-pair key
   int sh_ra, sh_rb, sh_pa, sh_pb;
   unsigned long long m_read, m_pos;
 };
+
+// Occurrence-pair keys that do not fit one word (the partitioned path): hi =
+// read_a << rbits | read_b, lo = pos_a << (pbits + 1) | pos_b << 1 | strand;
+// sorted by (hi, lo).
+struct __align__(16) Key2 {
+  unsigned long long lo, hi;
+};
+
+// Per key type: the sort tile (keys per block iteration of the radix passes)
+// and the 8-bit digit at bit `shift` (shift in [0, 64) for one word, [0, 128)
+// for two, never straddling a word: the passes run at multiples of 8 per word).
+template <typename K>
+struct KeyOps;
+template <>
+struct KeyOps<unsigned long long> {
+  static constexpr int kTile = 8192;
+  __device__ static unsigned digit(const unsigned long long& k, int shift) { return (unsigned)((k >> shift) & 255u); }
+};
+template <>
+struct KeyOps<Key2> {
+  static constexpr int kTile = 4096;
+  __device__ static unsigned digit(const Key2& k, int shift) {
+    return shift < 64 ? (unsigned)((k.lo >> shift) & 255u) : (unsigned)((k.hi >> (shift - 64)) & 255u);
+  }
+};
+
+// Fields of an occurrence-pair key (one word: the bit layout of KeyLayout; two
+// words: Key2 above with sh_pa / sh_pb in lo and sh_ra / sh_rb in hi).
+__device__ __forceinline__ unsigned long long make_key(const KeyLayout& kl, unsigned long long ra,
+                                                       unsigned long long rb, unsigned long long pa,
+                                                       unsigned long long pb, unsigned long long strand,
+                                                       unsigned long long*) {
+  return (ra << kl.sh_ra) | (rb << kl.sh_rb) | (pa << kl.sh_pa) | (pb << kl.sh_pb) | strand;
+}
+__device__ __forceinline__ Key2 make_key(const KeyLayout& kl, unsigned long long ra, unsigned long long rb,
+                                         unsigned long long pa, unsigned long long pb, unsigned long long strand,
+                                         Key2*) {
+  Key2 k;
+  k.lo = (pa << kl.sh_pa) | (pb << kl.sh_pb) | strand;
+  k.hi = (ra << kl.sh_ra) | (rb << kl.sh_rb);
+  return k;
+}
+__device__ __forceinline__ unsigned long long run_of(const KeyLayout& kl, const unsigned long long& k) {
+  return k >> kl.sh_rb;
+}
+__device__ __forceinline__ unsigned long long run_of(const KeyLayout&, const Key2& k) { return k.hi; }
+__device__ __forceinline__ unsigned long long lo_word(const unsigned long long& k) { return k; }
+__device__ __forceinline__ unsigned long long lo_word(const Key2& k) { return k.lo; }
+__device__ __forceinline__ unsigned long long hi_word(const unsigned long long& k) { return k; }
+__device__ __forceinline__ unsigned long long hi_word(const Key2& k) { return k.hi; }
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
   x ^= x >> 33;
@@ -296,18 +349,20 @@ __global__ void cap_keys_kernel(CandState* st, unsigned long long capacity) {
 
 // ---- LSD radix sort of 64-bit keys (8-bit digits) ------------------------
 
-__global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, const unsigned long long* n_ptr,
-                                  int shift, unsigned int* hist, unsigned long long n_tiles_max) {
+template <typename K>
+__global__ void digit_hist_kernel(const K* __restrict__ keys, const unsigned long long* n_ptr, int shift,
+                                  unsigned int* hist, unsigned long long n_tiles_max) {
+  constexpr int kT = KeyOps<K>::kTile;
   __shared__ unsigned int h[256];
   const unsigned long long n = *n_ptr;
-  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  const unsigned long long n_tiles = (n + kT - 1) / kT;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles && tile < n_tiles_max; tile += gridDim.x) {
     h[threadIdx.x] = 0;
     __syncthreads();
-    const unsigned long long t0 = tile * kTile;
-    for (int j = 0; j < kSortItems; ++j) {
+    const unsigned long long t0 = tile * kT;
+    for (int j = 0; j < kT / kSortThreads; ++j) {
       const unsigned long long i = t0 + (unsigned long long)j * kSortThreads + threadIdx.x;
-      if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+      if (i < n) atomicAdd(&h[KeyOps<K>::digit(keys[i], shift)], 1u);
     }
     __syncthreads();
     hist[(unsigned long long)threadIdx.x * n_tiles + tile] = h[threadIdx.x];
@@ -316,13 +371,15 @@ __global__ void digit_hist_kernel(const unsigned long long* __restrict__ keys, c
 }
 
 // Exclusive scan of len u32 counts into u64 offsets; len is fixed_len, or from
-// *n_ptr: 256 digit counts per tile (mode 1), one per tile (mode 2).  Two
+// *n_ptr: 256 digit counts per sort tile of `tile` keys (mode 1), one per
+// kTile keys (mode 2).  Two
 // launches of kScanBlocks blocks: each block sums its contiguous segment
 // (scan_reduce_kernel), then scans it from the sum of the segments before it
 // (scan_apply_kernel).  Both read the counts coalesced.
 __device__ __forceinline__ unsigned long long scan_len(const unsigned long long* n_ptr, int mode,
                                                        unsigned long long fixed_len) {
-  if (mode == 1) return 256ull * ((*n_ptr + kTile - 1) / kTile);
+  // mode 1: fixed_len holds the sort tile
+  if (mode == 1) return 256ull * ((*n_ptr + fixed_len - 1) / fixed_len);
   if (mode == 2) return (*n_ptr + kTile - 1) / kTile;
   return fixed_len;
 }
@@ -408,11 +465,15 @@ void scan_counts(const unsigned int* counts, unsigned long long* offsets, const 
 constexpr int kScatterThreads = 256;
 constexpr int kScatterBlocksPerSM = 2;
 constexpr int kScatterWarps = kScatterThreads / 32;
-constexpr int kWarpKeys = kTile / kScatterWarps;
-constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 2 + (size_t)kScatterWarps * 256 * 4 + 256 * 8 +
-                                256 * 4;
-static_assert(kTile <= 65536, "tile indices are 16-bit");
-static_assert(kScatterBlocksPerSM * (kScatterSmem + 1024) <= 228 * 1024, "scatter tiles do not fit shared memory");
+template <typename K>
+constexpr size_t scatter_smem() {
+  return (size_t)KeyOps<K>::kTile * sizeof(K) + (size_t)KeyOps<K>::kTile * 2 + (size_t)kScatterWarps * 256 * 4 +
+         256 * 8 + 256 * 4;
+}
+static_assert(KeyOps<unsigned long long>::kTile <= 65536 && KeyOps<Key2>::kTile <= 65536, "tile indices are 16-bit");
+static_assert(kScatterBlocksPerSM * (scatter_smem<unsigned long long>() + 1024) <= 228 * 1024 &&
+                  kScatterBlocksPerSM * (scatter_smem<Key2>() + 1024) <= 228 * 1024,
+              "scatter tiles do not fit shared memory");
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, unsigned src_bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -422,27 +483,31 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src,
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+template <typename K>
 __global__ void __launch_bounds__(kScatterThreads, kScatterBlocksPerSM)
-    digit_scatter_kernel(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out,
-                         const unsigned long long* n_ptr, int shift, const unsigned long long* offsets,
-                         unsigned int* status) {
+    digit_scatter_kernel(const K* __restrict__ in, K* __restrict__ out, const unsigned long long* n_ptr, int shift,
+                         const unsigned long long* offsets, unsigned int* status) {
+  constexpr int kT = KeyOps<K>::kTile;
+  constexpr int kWarpKeys = kT / kScatterWarps;
+  constexpr int kPerChunk = 16 / (int)sizeof(K);  // keys per 16-byte copy
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long* skey = (unsigned long long*)smem;                           // the tile, input order
-  unsigned short* inv = (unsigned short*)(smem + (size_t)kTile * 8);             // sorted slot -> input index
-  unsigned int* wcnt = (unsigned int*)(smem + (size_t)kTile * 10);               // [warp][digit]
+  K* skey = (K*)smem;                                                              // the tile, input order
+  unsigned short* inv = (unsigned short*)(smem + (size_t)kT * sizeof(K));          // sorted slot -> input index
+  unsigned int* wcnt = (unsigned int*)(smem + (size_t)kT * (sizeof(K) + 2));       // [warp][digit]
   unsigned long long* gbase = (unsigned long long*)(wcnt + kScatterWarps * 256);  // digit's first output slot
   unsigned int* lstart = (unsigned int*)(gbase + 256);                           // digit's first slot in the tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const unsigned long long n = *n_ptr;
-  const unsigned long long n_tiles = (n + kTile - 1) / kTile;
+  const unsigned long long n_tiles = (n + kT - 1) / kT;
   const int w0 = warp * kWarpKeys;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const unsigned long long t0 = tile * kTile;
-    const int m = n - t0 < (unsigned long long)kTile ? (int)(n - t0) : kTile;
-    for (int c = threadIdx.x; c < kTile / 2; c += kScatterThreads) {
-      const int e = 2 * c;  // a 16-byte chunk: keys e and e + 1, zero-filled past the tile's end
-      const unsigned bytes = e >= m ? 0u : (e + 1 < m ? 16u : 8u);
+    const unsigned long long t0 = tile * kT;
+    const int m = n - t0 < (unsigned long long)kT ? (int)(n - t0) : kT;
+    for (int c = threadIdx.x; c < kT / kPerChunk; c += kScatterThreads) {
+      const int e = kPerChunk * c;  // a 16-byte chunk: keys e .. e + kPerChunk - 1, zero-filled past the tile's end
+      const int valid = m - e < kPerChunk ? (m - e > 0 ? m - e : 0) : kPerChunk;
+      const unsigned bytes = (unsigned)valid * (unsigned)sizeof(K);
       cp_async16(skey + e, bytes ? (const void*)(in + t0 + e) : (const void*)in, bytes);
     }
     for (int x = threadIdx.x; x < kScatterWarps * 256; x += kScatterThreads) wcnt[x] = 0;
@@ -450,7 +515,7 @@ __global__ void __launch_bounds__(kScatterThreads, kScatterBlocksPerSM)
     __syncthreads();
     for (int r = 0; r < kWarpKeys; r += 32) {
       const int i = w0 + r + lane;
-      if (i < m) atomicAdd(&wcnt[warp * 256 + (unsigned)((skey[i] >> shift) & 255u)], 1u);
+      if (i < m) atomicAdd(&wcnt[warp * 256 + KeyOps<K>::digit(skey[i], shift)], 1u);
     }
     __syncthreads();
     if (threadIdx.x < 256) {  // thread d: prefix of digit d over the warps, and its tile count
@@ -488,19 +553,19 @@ __global__ void __launch_bounds__(kScatterThreads, kScatterBlocksPerSM)
     for (int r = 0; r < kWarpKeys; r += 32) {
       const int i = w0 + r + lane;
       const bool ok = i < m;
-      const unsigned d = ok ? (unsigned)((skey[i] >> shift) & 255u) : 256u;
+      const unsigned d = ok ? KeyOps<K>::digit(skey[i], shift) : 256u;
       const unsigned peers = __match_any_sync(kFullMask, d);
       const unsigned rank = __popc(peers & lt);
       const unsigned c = ok ? next[d] : 0u;
       __syncwarp();
       if (ok && rank == 0) next[d] = c + __popc(peers);
       __syncwarp();
-      if (ok && c + rank < (unsigned)kTile) inv[c + rank] = (unsigned short)i;
+      if (ok && c + rank < (unsigned)kT) inv[c + rank] = (unsigned short)i;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < m; q += kScatterThreads) {
-      const unsigned long long key = skey[inv[q] & (kTile - 1)];
-      const unsigned d = (unsigned)((key >> shift) & 255u);
+      const K key = skey[inv[q] & (kT - 1)];
+      const unsigned d = KeyOps<K>::digit(key, shift);
       const unsigned long long g = gbase[d] + (unsigned long long)(q - (int)lstart[d]);
       if (g < n)
         out[g] = key;
@@ -509,6 +574,27 @@ __global__ void __launch_bounds__(kScatterThreads, kScatterBlocksPerSM)
     }
     __syncthreads();  // the next tile reuses shared memory
   }
+}
+
+cudaError_t set_scatter_smem() {
+  cudaError_t e = cudaFuncSetAttribute(digit_scatter_kernel<unsigned long long>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)scatter_smem<unsigned long long>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(digit_scatter_kernel<Key2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<Key2>());
+  return e;
+}
+
+// One stable LSD pass by the digit at `shift`: histogram, scan, scatter.
+template <typename K>
+void radix_pass(const K* src, K* dst, const unsigned long long* n_ptr, int shift, unsigned int* hist,
+                unsigned long long* hoff, unsigned long long tiles_max, unsigned long long* part,
+                unsigned int* status, int sms, cudaStream_t st) {
+  digit_hist_kernel<K><<<sms * 8, 256, 0, st>>>(src, n_ptr, shift, hist, tiles_max);
+  scan_counts(hist, hoff, n_ptr, 1, (unsigned long long)KeyOps<K>::kTile, part, st);
+  digit_scatter_kernel<K><<<sms * kScatterBlocksPerSM, kScatterThreads, scatter_smem<K>(), st>>>(
+      src, dst, n_ptr, shift, hoff, status);
 }
 
 // ---- sort-based count (when code and occurrence index share 64 bits) ----------
@@ -555,12 +641,14 @@ __global__ void extract_kernel(StoreRef sr, const unsigned long long* off, int i
   }
 }
 
-// A thread per run of equal codes in the sorted occurrences: the multiplicity,
-// and for a retained k-mer its occurrence pairs (as in emit_pairs_kernel).
+// A thread per run of equal codes in the sorted occurrences (n_ptr of them):
+// the multiplicity, and for a retained k-mer its occurrence pairs (as in
+// emit_pairs_kernel), as one-word or two-word keys.
+template <typename K>
 __global__ void run_emit_kernel(const unsigned long long* __restrict__ sorted, const unsigned long long* info, int ib,
-                                int mult_lo, int mult_hi, KeyLayout kl, unsigned long long* keys_out,
-                                unsigned long long capacity, CandState* st) {
-  const unsigned long long n = st->instances;
+                                int mult_lo, int mult_hi, KeyLayout kl, K* keys_out,
+                                unsigned long long capacity, const unsigned long long* n_ptr, CandState* st) {
+  const unsigned long long n = *n_ptr;
   const unsigned long long imask = (1ull << ib) - 1ull;
   const unsigned long long lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -607,15 +695,71 @@ __global__ void run_emit_kernel(const unsigned long long* __restrict__ sorted, c
         if (ra == rb) continue;
         const unsigned long long pa = (v[x] >> 1) & 0x7FFFFFFFull, pb = (v[y] >> 1) & 0x7FFFFFFFull;
         const unsigned long long strand = (v[x] ^ v[y]) & 1ull;
-        keys_out[o++] = (ra << kl.sh_ra) | (rb << kl.sh_rb) | (pa << kl.sh_pa) | (pb << kl.sh_pb) | strand;
+        keys_out[o++] = make_key(kl, ra, rb, pa, pb, strand, (K*)nullptr);
       }
   }
+}
+
+// The partitioned count: one pass per hash part of the canonical codes.  Every
+// occurrence whose code falls in part `part` of n_parts is appended (one
+// warp-aggregated atomic per 32 positions) as (code << ib | slot) with its
+// read, position and orientation under that slot; the order within a pass is
+// free, since each run is ordered by (read, position) before its pairs are
+// formed and the pairs are sorted afterwards.
+__device__ __forceinline__ unsigned part_of(unsigned long long code, unsigned n_parts) {
+  return (unsigned)__umul64hi(mix64(code + 0x9E3779B97F4A7C15ull), (unsigned long long)n_parts);
+}
+
+__global__ void extract_part_kernel(StoreRef sr, unsigned part, unsigned n_parts, int ib, unsigned long long cap,
+                                    unsigned long long* keys, unsigned long long* info, CandState* st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = warp; r < sr.n_reads; r += n_warps) {
+    const long long len = sr.lengths[r];
+    const long long first = sr.word_offsets[r] * 16;
+    for (long long p0 = 0; p0 + sr.k <= len; p0 += 32) {  // uniform over the warp
+      const long long p = p0 + lane;
+      unsigned orient = 0;
+      unsigned long long c = 0;
+      bool mine = false;
+      if (p + sr.k <= len) {
+        c = canonical(bases_le(sr.words, first + p, sr.k), sr.k, &orient);
+        mine = part_of(c, n_parts) == part;
+      }
+      const unsigned bal = __ballot_sync(kFullMask, mine);
+      if (!bal) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&st->pass_count, (unsigned long long)__popc(bal));
+      base = __shfl_sync(kFullMask, base, 0);
+      if (!mine) continue;
+      const unsigned long long idx = base + __popc(bal & lt);
+      if (idx >= cap) {
+        atomicOr(&st->status, 8u);
+        continue;
+      }
+      keys[idx] = (c << ib) | idx;
+      info[idx] = ((unsigned long long)r << 32) | ((unsigned long long)p << 1) | orient;
+    }
+  }
+}
+
+// Per pass: the occurrences it holds (capped at the capacity, flagged in
+// status bit 3), their running total, and the largest pass so far.
+__global__ void pass_begin_kernel(CandState* st) { st->pass_count = 0; }
+__global__ void pass_end_kernel(CandState* st, unsigned long long cap) {
+  const unsigned long long c = st->pass_count;
+  st->instances += c;
+  if (c > st->max_pass) st->max_pass = c;
+  st->pass_held = c < cap ? c : cap;
 }
 
 // ---- seed selection and compaction -----------------------------------------
 
 // A thread per run start walks its run: selection flags and seed ids.
-__global__ void select_kernel(const unsigned long long* __restrict__ keys, CandState* st, KeyLayout kl,
+template <typename K>
+__global__ void select_kernel(const K* __restrict__ keys, CandState* st, KeyLayout kl,
                               int max_seeds, int gap, unsigned int* flags, unsigned int* sid) {
   const unsigned long long n = st->n_keys;
   const unsigned long long lane = threadIdx.x & 31;
@@ -623,14 +767,14 @@ __global__ void select_kernel(const unsigned long long* __restrict__ keys, CandS
   for (unsigned long long w0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w0 < n;
        w0 += stride) {
     const unsigned long long i = w0 + lane;
-    const bool start = i < n && (i == 0 || (keys[i - 1] >> kl.sh_rb) != (keys[i] >> kl.sh_rb));
+    const bool start = i < n && (i == 0 || run_of(kl, keys[i - 1]) != run_of(kl, keys[i]));
     warp_atomic_add(&st->candidates, start ? 1u : 0u);
     if (!start) continue;
-    const unsigned long long run = keys[i] >> kl.sh_rb;
+    const unsigned long long run = run_of(kl, keys[i]);
     int taken = 0;
     long long last = 0;
-    for (unsigned long long u = i; u < n && (keys[u] >> kl.sh_rb) == run; ++u) {
-      const long long pa = (long long)((keys[u] >> kl.sh_pa) & kl.m_pos);
+    for (unsigned long long u = i; u < n && run_of(kl, keys[u]) == run; ++u) {
+      const long long pa = (long long)((lo_word(keys[u]) >> kl.sh_pa) & kl.m_pos);
       const bool take = taken < max_seeds && (taken == 0 || pa >= last + gap);
       flags[u] = take ? 1u : 0u;
       sid[u] = take ? (unsigned)taken : 0u;
@@ -664,7 +808,8 @@ __global__ void tile_sum_kernel(const unsigned int* flags, const CandState* st, 
   }
 }
 
-__global__ void compact_kernel(const unsigned long long* __restrict__ keys, const unsigned int* flags,
+template <typename K>
+__global__ void compact_kernel(const K* __restrict__ keys, const unsigned int* flags,
                                const unsigned int* sid, const unsigned long long* tile_off, CandState* st,
                                KeyLayout kl, dibella_pair_t* out, unsigned long long capacity) {
   __shared__ unsigned int s[kSortThreads];
@@ -695,13 +840,14 @@ __global__ void compact_kernel(const unsigned long long* __restrict__ keys, cons
         ++o;
         continue;
       }
-      const unsigned long long key = keys[i];
+      const K key = keys[i];
+      const unsigned long long hw = hi_word(key), lw = lo_word(key);
       dibella_pair_t r;
-      r.read_a = (uint32_t)((key >> kl.sh_ra) & kl.m_read);
-      r.read_b = (uint32_t)((key >> kl.sh_rb) & kl.m_read);
-      r.pos_a = (uint32_t)((key >> kl.sh_pa) & kl.m_pos);
-      r.pos_b = (uint32_t)((key >> kl.sh_pb) & kl.m_pos);
-      r.strand = (uint8_t)(key & 1ull);
+      r.read_a = (uint32_t)((hw >> kl.sh_ra) & kl.m_read);
+      r.read_b = (uint32_t)((hw >> kl.sh_rb) & kl.m_read);
+      r.pos_a = (uint32_t)((lw >> kl.sh_pa) & kl.m_pos);
+      r.pos_b = (uint32_t)((lw >> kl.sh_pb) & kl.m_pos);
+      r.strand = (uint8_t)(lw & 1ull);
       r.pad[0] = r.pad[1] = r.pad[2] = 0;
       r.seed_id = sid[i];
       out[o++] = r;
@@ -721,6 +867,11 @@ __global__ void finish_kernel(CandState* st, const unsigned long long* tile_off,
   counts_out[3] = (int64_t)st->retained;
   counts_out[4] = (int64_t)st->occ_pairs;
   counts_out[5] = (int64_t)st->status;
+}
+
+// Partitioned path: counts_out[6] = the occurrences of the largest pass.
+__global__ void max_pass_kernel(const CandState* st, int64_t* counts_out) {
+  counts_out[6] = (int64_t)st->max_pass;
 }
 
 int bits_for(unsigned long long v) {  // bits needed for values 0..v
@@ -784,9 +935,196 @@ CandLayout cand_layout(long long n_reads, long long n_bases, int k, int mult_hi)
   return L;
 }
 
+// Workspace of the partitioned path: one pass's occurrence keys (two
+// buffers) and words, the occurrence-pair keys (two-word when they do not fit
+// one word; two buffers), selection flags and seed ids, and the sort and scan
+// scratch.  pass_cap = occurrences one pass holds: n_bases / n_parts with a
+// quarter more for the unevenness of the hash parts, plus 2^16.
+struct PartLayout {
+  unsigned long long pass_cap, pairs, tiles;
+  bool wide;  // two-word occurrence-pair keys
+  size_t state, okeys0, okeys1, info, pk0, pk1, hist, hoff, flags, sid, tsum, toff, part, total;
+};
+
+unsigned long long part_capacity(long long n_bases, int n_parts) {
+  const unsigned long long per = ((unsigned long long)(n_bases > 0 ? n_bases : 1) + n_parts - 1) / n_parts;
+  return per + per / 4 + 65536;
+}
+
+PartLayout part_layout(long long n_bases, int n_parts, long long occ_pair_capacity, bool wide) {
+  PartLayout L;
+  L.pass_cap = part_capacity(n_bases, n_parts);
+  L.pairs = (unsigned long long)(occ_pair_capacity > 0 ? occ_pair_capacity : 1);
+  L.wide = wide;
+  const size_t ksz = wide ? sizeof(Key2) : 8;
+  const unsigned long long ktile = wide ? KeyOps<Key2>::kTile : KeyOps<unsigned long long>::kTile;
+  const unsigned long long otiles = (L.pass_cap + kTile - 1) / kTile, ptiles = (L.pairs + ktile - 1) / ktile;
+  L.tiles = otiles > ptiles ? otiles : ptiles;
+  const unsigned long long ctiles = (L.pairs + kTile - 1) / kTile;  // compaction tiles
+  size_t off = 0;
+  L.state = off;  off = align256(off + sizeof(CandState));
+  L.okeys0 = off; off = align256(off + 8 * L.pass_cap);
+  L.okeys1 = off; off = align256(off + 8 * L.pass_cap);
+  L.info = off;   off = align256(off + 8 * L.pass_cap);
+  L.pk0 = off;    off = align256(off + ksz * L.pairs);
+  L.pk1 = off;    off = align256(off + ksz * L.pairs);
+  L.hist = off;   off = align256(off + 4 * 256 * L.tiles);
+  L.hoff = off;   off = align256(off + 8 * 256 * L.tiles);
+  L.flags = off;  off = align256(off + 4 * L.pairs);
+  L.sid = off;    off = align256(off + 4 * L.pairs);
+  L.tsum = off;   off = align256(off + 4 * ctiles);
+  L.toff = off;   off = align256(off + 8 * ctiles);
+  L.part = off;   off = align256(off + 8 * kScanBlocks);
+  L.total = off;
+  return L;
+}
+
+// Occurrence-pair keys are two words when read, read, position, position and
+// strand need more than 64 bits.
+bool wide_pair_keys(long long n_reads, int max_read_len) {
+  const int rbits = bits_for(n_reads > 0 ? (unsigned long long)(n_reads - 1) : 0);
+  const int pbits = bits_for(max_read_len > 0 ? (unsigned long long)max_read_len : 0);
+  return 2 * rbits + 2 * pbits + 1 > 64;
+}
+
+// Selection, compaction and counts over the sorted occurrence-pair keys.
+template <typename K>
+void select_and_compact(const K* keys, CandState* state, const KeyLayout& kl, int max_seeds, int gap,
+                        unsigned int* flags, unsigned int* sid, unsigned int* tsum, unsigned long long* toff,
+                        unsigned long long* part, dibella_pair_t* pairs_out, long long pairs_capacity,
+                        int64_t* counts_out, int sms, cudaStream_t st) {
+  const int sort_blocks = sms * 8;
+  select_kernel<K><<<sms * 8, 256, 0, st>>>(keys, state, kl, max_seeds, gap, flags, sid);
+  tile_sum_kernel<<<sort_blocks, kSortThreads, 0, st>>>(flags, state, tsum);
+  scan_counts(tsum, toff, &state->n_keys, 2, 0, part, st);
+  compact_kernel<K><<<sort_blocks, kSortThreads, 0, st>>>(keys, flags, sid, toff, state, kl, pairs_out,
+                                                          (unsigned long long)pairs_capacity);
+  finish_kernel<<<1, 1, 0, st>>>(state, toff, tsum, counts_out);
+}
+
 }  // namespace
 
 extern "C" {
+
+int dibella_candidate_workspace_bytes_parts(int64_t n_reads, int64_t n_bases, int32_t max_read_len, int32_t k,
+                                            int32_t n_parts, int64_t occ_pair_capacity, int64_t* bytes_out) {
+  if (!bytes_out || n_reads < 0 || n_bases < 0 || k < 1 || k > 32 || n_parts < 1 || n_parts > 4096 ||
+      occ_pair_capacity < 0 || occ_pair_capacity > (1ll << 40) || max_read_len < 0 ||
+      max_read_len > DIBELLA_MAX_READ_LEN)
+    return DIBELLA_EINVAL;
+  *bytes_out = (int64_t)part_layout(n_bases, n_parts, occ_pair_capacity, wide_pair_keys(n_reads, max_read_len)).total;
+  return DIBELLA_OK;
+}
+
+int dibella_candidate_pairs_parts(const uint32_t* packed_words, const int64_t* read_word_offsets,
+                                  const int32_t* read_lengths, int64_t n_reads, int64_t n_bases, int32_t max_read_len,
+                                  int32_t k, int32_t mult_lo, int32_t mult_hi, int32_t max_seeds,
+                                  int32_t min_seed_gap, int32_t n_parts, int64_t occ_pair_capacity,
+                                  dibella_pair_t* pairs_out, int64_t pairs_capacity, int64_t* counts_out,
+                                  void* workspace, int64_t workspace_bytes, void* stream) {
+  if (n_reads < 0 || n_bases < 0 || k < 1 || k > 32 || mult_lo < 1 || mult_hi < mult_lo || mult_hi > kMaxMult ||
+      max_seeds < 1 || min_seed_gap < 0 || max_read_len < 0 || max_read_len > DIBELLA_MAX_READ_LEN ||
+      n_parts < 1 || n_parts > 4096 || occ_pair_capacity < 0 || occ_pair_capacity > (1ll << 40) ||
+      pairs_capacity < 0 || !counts_out || !workspace || ((uintptr_t)workspace & 255))
+    return DIBELLA_EINVAL;
+  if (n_reads > 0 && (!packed_words || !read_word_offsets || !read_lengths)) return DIBELLA_EINVAL;
+  if (pairs_capacity > 0 && !pairs_out) return DIBELLA_EINVAL;
+  if (n_reads > (1ll << 32)) return DIBELLA_EINVAL;  // read ids are 32-bit
+  const int rbits = bits_for(n_reads > 0 ? (unsigned long long)(n_reads - 1) : 0);
+  const int pbits = bits_for(max_read_len > 0 ? (unsigned long long)max_read_len : 0);
+  const bool wide = 2 * rbits + 2 * pbits + 1 > 64;
+  const PartLayout L = part_layout(n_bases, n_parts, occ_pair_capacity, wide);
+  // a pass keys each occurrence by (code << ib | slot): both must fit 64 bits
+  const int ib = bits_for(L.pass_cap);
+  if (2 * k + ib > 64) return DIBELLA_EINVAL;
+  if ((unsigned long long)workspace_bytes < L.total) return DIBELLA_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  CandState* state = (CandState*)(ws + L.state);
+  unsigned long long* ok0 = (unsigned long long*)(ws + L.okeys0);
+  unsigned long long* ok1 = (unsigned long long*)(ws + L.okeys1);
+  unsigned long long* info = (unsigned long long*)(ws + L.info);
+  unsigned int* hist = (unsigned int*)(ws + L.hist);
+  unsigned long long* hoff = (unsigned long long*)(ws + L.hoff);
+  unsigned int* flags = (unsigned int*)(ws + L.flags);
+  unsigned int* sid = (unsigned int*)(ws + L.sid);
+  unsigned int* tsum = (unsigned int*)(ws + L.tsum);
+  unsigned long long* toff = (unsigned long long*)(ws + L.toff);
+  unsigned long long* part = (unsigned long long*)(ws + L.part);
+
+  KeyLayout kl;
+  kl.sh_pb = 1;
+  kl.sh_pa = 1 + pbits;
+  kl.m_read = (1ull << rbits) - 1ull;
+  kl.m_pos = (1ull << pbits) - 1ull;
+  if (wide) {  // lo = pa | pb | strand, hi = ra | rb
+    kl.sh_rb = 0;
+    kl.sh_ra = rbits;
+  } else {
+    kl.sh_rb = 1 + 2 * pbits;
+    kl.sh_ra = 1 + 2 * pbits + rbits;
+  }
+  cudaError_t e;
+  if ((e = set_scatter_smem()) != cudaSuccess) return DIBELLA_ECUDA;
+  if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  StoreRef sr{packed_words, read_word_offsets, read_lengths, (long long)n_reads, k};
+  for (int p = 0; p < n_parts && n_reads > 0; ++p) {
+    pass_begin_kernel<<<1, 1, 0, st>>>(state);
+    extract_part_kernel<<<sms * 16, 256, 0, st>>>(sr, (unsigned)p, (unsigned)n_parts, ib, L.pass_cap, ok0, info,
+                                                  state);
+    pass_end_kernel<<<1, 1, 0, st>>>(state, L.pass_cap);
+    unsigned long long* osrc = ok0;
+    unsigned long long* odst = ok1;
+    for (int j = 0; j < (2 * k + 7) / 8; ++j) {
+      radix_pass(osrc, odst, &state->pass_held, ib + 8 * j, hist, hoff, L.tiles, part, &state->status, sms, st);
+      unsigned long long* tmp = osrc;
+      osrc = odst;
+      odst = tmp;
+    }
+    if (wide)
+      run_emit_kernel<Key2><<<sms * 8, 256, 0, st>>>(osrc, info, ib, mult_lo, mult_hi, kl, (Key2*)(ws + L.pk0),
+                                                     L.pairs, &state->pass_held, state);
+    else
+      run_emit_kernel<unsigned long long><<<sms * 8, 256, 0, st>>>(osrc, info, ib, mult_lo, mult_hi, kl,
+                                                                   (unsigned long long*)(ws + L.pk0), L.pairs,
+                                                                   &state->pass_held, state);
+  }
+  cap_keys_kernel<<<1, 1, 0, st>>>(state, L.pairs);
+  const int gap = min_seed_gap > 0 ? min_seed_gap : k;
+  if (wide) {
+    Key2* src = (Key2*)(ws + L.pk0);
+    Key2* dst = (Key2*)(ws + L.pk1);
+    const int lo_bits = 1 + 2 * pbits, hi_bits = 2 * rbits;
+    for (int j = 0; j < (lo_bits + 7) / 8 + (hi_bits + 7) / 8; ++j) {
+      const int shift = j < (lo_bits + 7) / 8 ? 8 * j : 64 + 8 * (j - (lo_bits + 7) / 8);
+      radix_pass(src, dst, &state->n_keys, shift, hist, hoff, L.tiles, part, &state->status, sms, st);
+      Key2* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    select_and_compact(src, state, kl, max_seeds, gap, flags, sid, tsum, toff, part, pairs_out, pairs_capacity,
+                       counts_out, sms, st);
+  } else {
+    unsigned long long* src = (unsigned long long*)(ws + L.pk0);
+    unsigned long long* dst = (unsigned long long*)(ws + L.pk1);
+    const int passes = (kl.sh_ra + rbits + 7) / 8;
+    for (int j = 0; j < passes; ++j) {
+      radix_pass(src, dst, &state->n_keys, 8 * j, hist, hoff, L.tiles, part, &state->status, sms, st);
+      unsigned long long* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    select_and_compact(src, state, kl, max_seeds, gap, flags, sid, tsum, toff, part, pairs_out, pairs_capacity,
+                       counts_out, sms, st);
+  }
+  max_pass_kernel<<<1, 1, 0, st>>>(state, counts_out);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DIBELLA_OK : DIBELLA_ECUDA;
+}
 
 int dibella_candidate_workspace_bytes(int64_t n_reads, int64_t n_bases, int32_t k, int32_t mult_hi,
                                       int64_t* bytes_out) {
@@ -840,9 +1178,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   kl.m_pos = (1ull << pbits) - 1ull;
 
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(digit_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kScatterSmem)) != cudaSuccess)
-    return DIBELLA_ECUDA;
+  if ((e = set_scatter_smem()) != cudaSuccess) return DIBELLA_ECUDA;
   if ((e = cudaMemsetAsync(state, 0, sizeof(CandState), st)) != cudaSuccess) return DIBELLA_ECUDA;
   if (!L.sort && (e = cudaMemsetAsync(t.slots, 0, sizeof(Slot) * L.slots, st)) != cudaSuccess) return DIBELLA_ECUDA;
   int dev = 0, sms = 0;
@@ -868,15 +1204,13 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
     unsigned long long* osrc = ok0;
     unsigned long long* odst = ok1;
     for (int j = 0; j < (2 * k + 7) / 8; ++j) {
-      digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(osrc, &state->instances, ib + 8 * j, hist, L.tiles);
-      scan_counts(hist, hoff, &state->instances, 1, 0, part, st);
-      digit_scatter_kernel<<<sms * kScatterBlocksPerSM, kScatterThreads, kScatterSmem, st>>>(
-          osrc, odst, &state->instances, ib + 8 * j, hoff, &state->status);
+      radix_pass(osrc, odst, &state->instances, ib + 8 * j, hist, hoff, L.tiles, part, &state->status, sms, st);
       unsigned long long* tmp = osrc;
       osrc = odst;
       odst = tmp;
     }
-    run_emit_kernel<<<sms * 8, 256, 0, st>>>(osrc, info, ib, mult_lo, mult_hi, kl, pk0, L.pairs, state);
+    run_emit_kernel<<<sms * 8, 256, 0, st>>>(osrc, info, ib, mult_lo, mult_hi, kl, pk0, L.pairs, &state->instances,
+                                             state);
   } else if (n_reads > 0) {
     kmer_walk_kernel<false><<<walk_blocks, 256, 0, st>>>(sr, t, inst, L.inst, mult_lo, mult_hi, state);
     allocate_kernel<<<sms * 8, 256, 0, st>>>(t, L.slots, mult_lo, mult_hi, retained, state);
@@ -890,10 +1224,7 @@ int dibella_candidate_pairs(const uint32_t* packed_words, const int64_t* read_wo
   unsigned long long* src = pk0;
   unsigned long long* dst = pk1;
   for (int pss = 0; pss < passes; ++pss) {
-    digit_hist_kernel<<<sort_blocks, 256, 0, st>>>(src, &state->n_keys, 8 * pss, hist, L.tiles);
-    scan_counts(hist, hoff, &state->n_keys, 1, 0, part, st);
-    digit_scatter_kernel<<<sms * kScatterBlocksPerSM, kScatterThreads, kScatterSmem, st>>>(
-        src, dst, &state->n_keys, 8 * pss, hoff, &state->status);
+    radix_pass(src, dst, &state->n_keys, 8 * pss, hist, hoff, L.tiles, part, &state->status, sms, st);
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;

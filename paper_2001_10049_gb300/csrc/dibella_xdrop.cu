@@ -71,7 +71,8 @@ static_assert(sizeof(ExtOut) == 24, "ext out is 24 bytes");
 // Queues: routed narrow / wide; narrow escalations (to the wide form); one
 // queue per step of the wide-form slot ladder (8 -> 16 -> 24 -> 32 slots);
 // the shared-memory form's input; the global-band form's input.
-enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQLadder = 3, kQSmem = 7, kQGlobal = 8, kNumQ = 9 };
+// The mid form's escalations (extensions whose band outgrew it) go to kQEsc2.
+enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQLadder = 3, kQSmem = 7, kQGlobal = 8, kQEsc2 = 9, kNumQ = 10 };
 
 struct Counters {
   unsigned int tail[kNumQ];   // queue sizes (see the kQ* names)
@@ -80,10 +81,11 @@ struct Counters {
   unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
   unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / wide /
-                          // shared-memory form, band overflows
+                          // shared-memory form, band overflows, escalated from the mid form
   // cells of finished extensions: 0 narrow, 1 wide (first launch), 2 CTA,
-  // 3 global, 4 wide launch on the narrow escalations, 5 slot-ladder rungs
-  unsigned long long cells[6];
+  // 3 global, 4 wide launch on the narrow escalations, 5 slot-ladder rungs,
+  // 6 mid form (the narrow escalations, one lane per extension, wide band)
+  unsigned long long cells[8];
 };
 
 
@@ -108,6 +110,8 @@ struct ExtendParams {
   // form above the ladder walks a wide band faster than one warp (0 = never).
   unsigned forward_max;
   int cells_idx;  // Counters::cells entry the wide forms add to
+  int narrow_cells_idx;  // Counters::cells entry of the one-lane forms (0 narrow, 6 mid)
+  int narrow_esc_stat;   // Counters::stat entry counting their escalations (2 narrow, 6 mid)
   Scoring sc;
   int* gband;
   int gcap;
@@ -1371,9 +1375,14 @@ __global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
 }
 
 // Narrow form: one lane per extension; lanes refill independently.  Each warp
-// owns 2*WT*32 cells of type T in shared memory (see NarrowLane).
-template <int WT, typename T>
-__global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
+// owns 2*WT*32 cells of type T in shared memory (see NarrowLane).  The same
+// kernel with a wide row (WT = 128..256, one warp per block so that the rows
+// of more warps fit an SM) is the mid form: it takes the narrow form's
+// escalations, whose bands (about 100-200 cells for reads that share their
+// seed by chance) a lane walks for ~12 warp instructions per 32 cells, against
+// a fixed per-antidiagonal control cost for a whole warp per extension.
+template <int WT, typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
   extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
   T* wbase = reinterpret_cast<T*>(smem_words) + (threadIdx.x >> 5) * (2 * WT * 32);
@@ -1415,12 +1424,12 @@ __global__ void __launch_bounds__(kBlockThreads) narrow_kernel(ExtendParams p) {
         ExtOut o;
         o.best = L.best; o.i_end = L.bi; o.j_end = L.bj; o.status = 0; o.cells = L.cells;
         p.ext[L.item] = o;
-        atomicAdd(&p.cnt->cells[0], (unsigned long long)L.cells);
+        atomicAdd(&p.cnt->cells[p.narrow_cells_idx], (unsigned long long)L.cells);
         active = false;
       } else if (r == 2) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
         p.esc_q[s] = L.item;
-        atomicAdd(&p.cnt->stat[2], 1u);
+        atomicAdd(&p.cnt->stat[p.narrow_esc_stat], 1u);
         active = false;
       }
     }
@@ -1661,12 +1670,13 @@ dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/30, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
-    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}};
+    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0};
 
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
   int narrow_blocks[2][3] = {};  // narrow_kernel<32/48/64, int | short> blocks per SM
+  int mid_blocks[3] = {};        // narrow_kernel<128/192/256, short, 1> (the mid form) blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
   int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
   int grp16_blocks[3] = {0, 0, 0};   // wide_grp_kernel<16, 16/24/32> blocks per SM
@@ -1725,9 +1735,9 @@ int gcap_from_workspace(long long n_pairs, long long bytes) {
   return best;
 }
 
-template <int WT, typename T>
+template <int WT, typename T, int NW>
 size_t narrow_smem() {
-  return (size_t)kWarpsPerBlock * 2 * WT * 32 * sizeof(T);
+  return (size_t)NW * 2 * WT * 32 * sizeof(T);
 }
 
 int occupancy(int* out, const void* fn, int threads, size_t smem) {
@@ -1752,18 +1762,24 @@ int device_info(DeviceInfo** out) {
     e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     int rc = DIBELLA_OK;
-    if ((rc = occupancy(&D.narrow_blocks[0][0], (const void*)narrow_kernel<32, int>, kBlockThreads,
-                        narrow_smem<32, int>())) ||
-        (rc = occupancy(&D.narrow_blocks[0][1], (const void*)narrow_kernel<48, int>, kBlockThreads,
-                        narrow_smem<48, int>())) ||
-        (rc = occupancy(&D.narrow_blocks[0][2], (const void*)narrow_kernel<64, int>, kBlockThreads,
-                        narrow_smem<64, int>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][0], (const void*)narrow_kernel<32, short>, kBlockThreads,
-                        narrow_smem<32, short>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][1], (const void*)narrow_kernel<48, short>, kBlockThreads,
-                        narrow_smem<48, short>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][2], (const void*)narrow_kernel<64, short>, kBlockThreads,
-                        narrow_smem<64, short>())) ||
+    if ((rc = occupancy(&D.narrow_blocks[0][0], (const void*)narrow_kernel<32, int, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<32, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][1], (const void*)narrow_kernel<48, int, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<48, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][2], (const void*)narrow_kernel<64, int, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<64, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0], (const void*)narrow_kernel<32, short, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<32, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1], (const void*)narrow_kernel<48, short, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<48, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2], (const void*)narrow_kernel<64, short, kWarpsPerBlock>, kBlockThreads,
+                        narrow_smem<64, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.mid_blocks[0], (const void*)narrow_kernel<128, short, 1>, 32,
+                        narrow_smem<128, short, 1>())) ||
+        (rc = occupancy(&D.mid_blocks[1], (const void*)narrow_kernel<192, short, 1>, 32,
+                        narrow_smem<192, short, 1>())) ||
+        (rc = occupancy(&D.mid_blocks[2], (const void*)narrow_kernel<256, short, 1>, 32,
+                        narrow_smem<256, short, 1>())) ||
         (rc = occupancy(&D.reg_blocks[0], (const void*)wide_reg_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.reg_blocks[1], (const void*)wide_reg_kernel<32>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.pk_blocks[0], (const void*)wide_pk_kernel<16>, kBlockThreads, 0)) ||
@@ -1785,6 +1801,8 @@ int device_info(DeviceInfo** out) {
 
 int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
+  if (s.mid_band_cap != 0 && s.mid_band_cap != 128 && s.mid_band_cap != 192 && s.mid_band_cap != 256)
+    return DIBELLA_EINVAL;
   if (s.wide_slots != 0 && s.wide_slots != 8 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32)
     return DIBELLA_EINVAL;
   if (s.wide_slots == 8 && s.wide_group_lanes != 0 && s.wide_group_lanes != 32) return DIBELLA_EINVAL;
@@ -1835,19 +1853,33 @@ inline int narrow_kind(int xdrop) { return xdrop <= kNarrow16MaxX ? 1 : 0; }
 cudaError_t launch_narrow(int wt, int xdrop, int grid, cudaStream_t st, const ExtendParams& ep) {
   if (narrow_kind(xdrop)) {
     if (wt == 32)
-      narrow_kernel<32, short><<<grid, kBlockThreads, narrow_smem<32, short>(), st>>>(ep);
+      narrow_kernel<32, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>(), st>>>(ep);
     else if (wt == 48)
-      narrow_kernel<48, short><<<grid, kBlockThreads, narrow_smem<48, short>(), st>>>(ep);
+      narrow_kernel<48, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>(), st>>>(ep);
     else
-      narrow_kernel<64, short><<<grid, kBlockThreads, narrow_smem<64, short>(), st>>>(ep);
+      narrow_kernel<64, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>(), st>>>(ep);
   } else {
     if (wt == 32)
-      narrow_kernel<32, int><<<grid, kBlockThreads, narrow_smem<32, int>(), st>>>(ep);
+      narrow_kernel<32, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<32, int, kWarpsPerBlock>(), st>>>(ep);
     else if (wt == 48)
-      narrow_kernel<48, int><<<grid, kBlockThreads, narrow_smem<48, int>(), st>>>(ep);
+      narrow_kernel<48, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<48, int, kWarpsPerBlock>(), st>>>(ep);
     else
-      narrow_kernel<64, int><<<grid, kBlockThreads, narrow_smem<64, int>(), st>>>(ep);
+      narrow_kernel<64, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<64, int, kWarpsPerBlock>(), st>>>(ep);
   }
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// The mid form (int16 cells only): one lane per extension, WT = 128/192/256.
+cudaError_t launch_mid(const DeviceInfo& D, int wt, cudaStream_t st, const ExtendParams& ep) {
+  const int vi = wt == 128 ? 0 : (wt == 192 ? 1 : 2);
+  const int grid = D.sms * D.mid_blocks[vi];
+  if (wt == 128)
+    narrow_kernel<128, short, 1><<<grid, 32, narrow_smem<128, short, 1>(), st>>>(ep);
+  else if (wt == 192)
+    narrow_kernel<192, short, 1><<<grid, 32, narrow_smem<192, short, 1>(), st>>>(ep);
+  else
+    narrow_kernel<256, short, 1><<<grid, 32, narrow_smem<256, short, 1>(), st>>>(ep);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -1908,15 +1940,19 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
 
 // All extension launches of one batch, in stream order:
 //   narrow form        on Narrow        (outgrown -> Esc1)
-//   wide form (S slots) on Wide, Esc1   (outgrown -> ladder queue of S)
+//   wide form (S slots) on Wide         (outgrown -> ladder queue of S)
+//   mid form           on Esc1          (outgrown -> Esc2; int16 cells only,
+//                                        skipped when the schedule has none)
+//   wide form (S slots) on Esc2 (or Esc1 without a mid form)
 //   wide form, next rung of the slot ladder 8 -> 16 -> 24 -> 32, on the queue
 //                      of the rung below (outgrown -> its own queue; the top
 //                      rung hands a short queue on unextended)
 //   CTA form           on Smem          (outgrown -> Global)
 //   global form        on Global
 // Every launch whose queue is empty returns at once.  Phase events: 2 after
-// the narrow launch, 3 after the first wide launch, 4 after the wide launch
-// on the narrow escalations, 5 after the ladder, CTA and global launches.
+// the narrow launch, 3 after the first wide launch, 4 after the mid form (at
+// once when there is none), 5 after the wide launch on the escalations, 6
+// after the ladder, CTA and global launches.
 int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, ExtendParams ep,
                       int* const q[kNumQ], cudaStream_t st) {
   dibella_schedule_t sch = sch_in;
@@ -1943,6 +1979,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.narrow_q_id = kQNarrow;
   ep.esc_q = q[kQEsc1];
   ep.esc_q_id = kQEsc1;
+  ep.narrow_cells_idx = 0;
+  ep.narrow_esc_stat = 2;
   if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
   record(st, 2);
 
@@ -1956,11 +1994,27 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.cells_idx = 1;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
   record(st, 3);
-  ep.wide_q = q[kQEsc1];
-  ep.wide_q_id = kQEsc1;
+  int esc_in = kQEsc1;
+  if (sch.mid_band_cap > 0 && narrow_kind(xdrop) == 1) {
+    const int wide_esc_q = ep.esc_q_id;
+    ep.narrow_q = q[kQEsc1];
+    ep.narrow_q_id = kQEsc1;
+    ep.esc_q = q[kQEsc2];
+    ep.esc_q_id = kQEsc2;
+    ep.narrow_cells_idx = 6;
+    ep.narrow_esc_stat = 6;
+    if ((e = launch_mid(D, sch.mid_band_cap, st, ep)) != cudaSuccess) return cuda_fail(e, "mid launch");
+    ep.narrow_q = nullptr;
+    ep.esc_q = q[wide_esc_q];
+    ep.esc_q_id = wide_esc_q;
+    esc_in = kQEsc2;
+  }
+  record(st, 4);
+  ep.wide_q = q[esc_in];
+  ep.wide_q_id = esc_in;
   ep.cells_idx = 4;
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
-  record(st, 4);
+  record(st, 5);
   ep.cells_idx = 5;
   for (int r = 0; r < n_rungs; ++r) {
     dibella_schedule_t up = sch;
@@ -1992,7 +2046,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
   ++g_launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
-  record(st, 5);
+  record(st, 6);
   return DIBELLA_OK;
 }
 
@@ -2055,35 +2109,26 @@ int finish(const int32_t* lens, const dibella_pair_t* pairs, int64_t n_pairs, in
 // Fixed scratch for dibella_xdrop_batch_noalloc.  Every GPU that loads this
 // library holds kNoAllocBytes of it until the process exits.  Host code must
 // not use the symbol's name as an address: it resolves the device address with
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, with the caller's device current, on every call (the
+// lookup is cheap once the module is loaded, and it stays right if the
+// context is destroyed and re-created and the module reloads elsewhere).
 constexpr long long kNoAllocMaxPairs = DIBELLA_NOALLOC_MAX_PAIRS;
 constexpr int kNoAllocBandCap = 8192;  // global-band cells per warp slot at the maximum batch
+static_assert(kNoAllocBandCap - 3 == DIBELLA_NOALLOC_MAX_BAND, "the band limit stated in include/dibella.h");
 constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kNoAllocBytes =
     up256(sizeof(Counters)) + up256(sizeof(Item) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(ExtOut) * 2 * kNoAllocMaxPairs) + kNumQ * up256(sizeof(int) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(int) * 3 * (size_t)kNoAllocBandCap * kGlobalWarps);
-static_assert(kNoAllocBytes == 9306624, "the size stated in include/dibella.h must follow the layout");
+static_assert(kNoAllocBytes == 9437696, "the size stated in include/dibella.h must follow the layout");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {};
-
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// Device address of the scratch array on the current device.
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= 64) return DIBELLA_EINVAL;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+  *out = p;
   return DIBELLA_OK;
 }
 
@@ -2182,7 +2227,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
   if (rc != DIBELLA_OK) return rc;
   rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
-  record(st, 6);
+  record(st, 7);
   return rc;
 }
 
@@ -2388,6 +2433,17 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       if (li == 0 && ci > 0) continue;  // all-wide ignores the narrow chunk
       rc = consider(c);
     }
+  // Stage 1b: the mid form's band (none, 128, 192 or 256 cells per lane).
+  {
+    const dibella_schedule_t base1b = cur;
+    const int mids[4] = {0, 128, 192, 256};
+    for (int mi = 0; mi < 4 && rc == DIBELLA_OK; ++mi) {
+      if (mids[mi] == base1b.mid_band_cap) continue;
+      dibella_schedule_t c = base1b;
+      c.mid_band_cap = mids[mi];
+      rc = consider(c);
+    }
+  }
   // Stage 2: lanes per extension (warp or 16/8-lane groups) x register slots of the wide form.
   {
     const dibella_schedule_t base2 = cur;
@@ -2462,11 +2518,11 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
   e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const int64_t v[12] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
+  const int64_t v[14] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
                          (int64_t)c.cells[0], (int64_t)(c.cells[1] + c.cells[4] + c.cells[5]),
                          (int64_t)c.cells[2], (int64_t)c.cells[3], (int64_t)c.cells[4],
-                         (int64_t)c.cells[5]};
-  int n = std::min(n_max, 12);
+                         (int64_t)c.cells[5], (int64_t)c.cells[6], c.stat[6]};
+  int n = std::min(n_max, 14);
   for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
 }

@@ -69,6 +69,50 @@ class ReadStore:
         return recs, stats
 
 
+    def candidate_pairs_parts(self, k: int = 17, mult_lo: int = 2, mult_hi: int = 8, max_seeds: int = 1,
+                              min_seed_gap: int = 0, n_parts: int = 1, occ_pair_capacity: int | None = None,
+                              pairs_capacity: int | None = None, max_read_len: int | None = None, stream=None,
+                              to_host: bool = True):
+        """dibella_candidate_pairs_parts: the same seed records, counted in
+        n_parts hash passes (for read sets beyond one sort key).  Synchronous:
+        returns (records, dict of counts); records are a numpy PAIR_DTYPE array,
+        or with to_host=False a device uint8 tensor of shape (seeds, 24)."""
+        from . import PAIR_DTYPE, dibella_candidate_pairs_parts, dibella_candidate_workspace_bytes_parts
+        torch = _torch()
+        dev = self.words.device
+        mrl = self.max_len if max_read_len is None else max_read_len
+        occ_cap = occ_pair_capacity
+        if occ_cap is None:
+            # The most occurrence pairs the multiplicity window allows, or as many
+            # as 85% of the free device memory holds (workspace plus one 24-byte
+            # output record per occurrence pair), whichever is smaller.
+            worst = max(1024, self.n_bases * (mult_hi - 1) // 2 + 1)
+            base = dibella_candidate_workspace_bytes_parts(self.n_reads, self.n_bases, mrl, k, n_parts, 0)
+            per = dibella_candidate_workspace_bytes_parts(self.n_reads, self.n_bases, mrl, k, n_parts, 1 << 20) - base
+            free = torch.cuda.mem_get_info(dev)[0]
+            fit = int((0.85 * free - base) / (per / float(1 << 20) + 24))
+            occ_cap = max(1024, min(worst, fit))
+        cap = pairs_capacity if pairs_capacity is not None else max(1024, occ_cap)
+        ws_bytes = dibella_candidate_workspace_bytes_parts(self.n_reads, self.n_bases, mrl, k, n_parts, occ_cap)
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        counts = torch.zeros(7, dtype=torch.int64, device=dev)
+        out = torch.empty((cap, 24), dtype=torch.uint8, device=dev)
+        dibella_candidate_pairs_parts(self.words, self.word_offsets, self.lengths, self.n_reads, self.n_bases, mrl, k,
+                                      mult_lo, mult_hi, max_seeds, min_seed_gap, n_parts, occ_cap, out, cap, counts,
+                                      workspace, ws_bytes, stream)
+        torch.cuda.synchronize(dev)
+        del workspace
+        c = counts.cpu().numpy()
+        stats = dict(zip(["seeds", "candidate_pairs", "instances", "retained_kmers", "occurrence_pairs", "status",
+                          "max_pass"], (int(v) for v in c)))
+        if stats["status"]:
+            raise RuntimeError("dibella_candidate_pairs_parts incomplete, status %d" % stats["status"])
+        recs = out[:stats["seeds"]]
+        if to_host:
+            recs = recs.cpu().numpy().reshape(-1).view(PAIR_DTYPE)
+        return recs, stats
+
+
 class Aligner:
     """Runs dibella_xdrop_batch on a ReadStore with a reusable workspace."""
 

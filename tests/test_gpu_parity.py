@@ -34,7 +34,8 @@ def test_c1_all_pairs(c1, X):
     assert ((got["status"] & 4) != 0).sum() == len(workloads.pair_groups(c1.pairs)) - 1
 
 
-@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "packed8", "packed16", "packed24", "packed32",
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "mid128", "mid192", "mid256", "nomid",
+                                  "packed8", "packed16", "packed24", "packed32",
                                   "int16", "int32", "grp16x16", "grp16x24", "grp16x32", "grp8x16", "grp8x24"])
 @pytest.mark.parametrize("X", [0, 3, 7, 25])
 def test_every_kernel_form_matches(c1, form, X):
@@ -46,6 +47,11 @@ def test_every_kernel_form_matches(c1, form, X):
         sched = schedule(wide_slots=int(form[6:]), wide_packed=1, wide_group_lanes=32, **WIDE_ALL)
     elif form.startswith("int"):
         sched = schedule(wide_slots=int(form[3:]), wide_packed=0, **WIDE_ALL)
+    elif form.startswith("mid"):
+        # every extension through the 32-cell narrow form, its escalations through the mid form
+        sched = schedule(narrow_band_cap=32, mid_band_cap=int(form[3:]), **NARROW_ALL)
+    elif form == "nomid":
+        sched = schedule(narrow_band_cap=32, mid_band_cap=0, **NARROW_ALL)
     else:
         sched = schedule(narrow_band_cap=int(form[6:]), **NARROW_ALL)
     pairs = c1.pairs[:300]
@@ -109,6 +115,8 @@ def test_fuzz_medium(scoring):
         sc = scoring + (X,)
         exp = oracle_align(ascii, offs, pairs, k, sc)
         for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL),
+                      schedule(narrow_band_cap=32, mid_band_cap=128, **NARROW_ALL),
+                      schedule(mid_band_cap=0, **NARROW_ALL),
                       schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, wide_group_lanes=32, **WIDE_ALL),
                       schedule(wide_group_lanes=16, **WIDE_ALL), schedule(wide_group_lanes=8, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
@@ -208,7 +216,7 @@ def test_counters_report_routing(c1):
     import paper_2001_10049_gb300 as dib
     store = dib.ReadStore.from_ascii(c1.reads, c1.offsets)
     al = dib.Aligner(store, len(c1.pairs), k=17)
-    al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, **NARROW_ALL))
+    al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, mid_band_cap=0, **NARROW_ALL))
     # expand, scan, scatter; narrow; wide twice; ladder 16/24/32; CTA; global; combine, best of pair
     assert dib.dibella_last_launch_count() == 13
     c = dib.dibella_batch_counters(al.workspace)
@@ -216,6 +224,17 @@ def test_counters_report_routing(c1):
     assert c["escalated_narrow"] > 0 and c["band_overflow"] == 0
     # the narrow escalations are finished by the wide launch on them (or above)
     assert c["cells_wide"] == c["cells_wide_esc"] + c["cells_ladder"] and c["cells_wide_esc"] > 0
+    assert c["cells_mid"] == 0 and c["escalated_mid"] == 0
+    # with the mid form (one more launch) it takes the narrow escalations first
+    al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, mid_band_cap=128,
+                                                                  **NARROW_ALL))
+    assert dib.dibella_last_launch_count() == 14
+    c2 = dib.dibella_batch_counters(al.workspace)
+    assert c2["escalated_narrow"] == c["escalated_narrow"] and c2["cells_mid"] > 0
+    assert c2["cells_wide_esc"] < c["cells_wide_esc"]
+    total = lambda d: sum(d[f] for f in ("cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_mid"))
+    # escalated extensions restart, so the finished cells of both runs agree
+    assert total(c2) == total(c)
 
 
 def test_c2_full_size_sampled():

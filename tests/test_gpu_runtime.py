@@ -112,3 +112,29 @@ def test_serving_admission_by_memory(c1, store):
     stats = srv.run(reqs, timeout_s=120)
     assert stats["max_inflight"] == 1
     assert all(r.done is not None for r in reqs)
+
+
+def test_serving_c5_shaped_requests_match_whole_batches():
+    """C5's request mix on the E. coli-sized store: Poisson arrivals of requests
+    of 1..4096 candidate pairs (log-uniform) with X drawn from {7, 25, 50},
+    admitted by device memory and overlapping on several streams.  Each served
+    result equals the same records of the whole batch aligned at that X in one
+    call (whole candidate pairs, so even the best-seed flags agree); the whole
+    batches are checked record by record against the oracle in
+    test_gpu_full_parity.py."""
+    import paper_2001_10049_gb300 as dib
+    from paper_2001_10049_gb300.serving import Request, Server
+    w = workloads.generate("c2_ecoli")
+    st = dib.ReadStore.from_ascii(w.reads, w.offsets)
+    specs = workloads.serving_requests(w.pairs, 48, rate_per_s=300.0, seed=45)
+    reqs = [Request(i, t, x, w.pairs[idx]) for i, (t, x, idx) in enumerate(specs)]
+    srv = Server(st, k=17, arena_bytes=2 << 30, max_batch=65536, n_streams=8)
+    stats = srv.run(reqs, timeout_s=600)
+    assert stats["requests"] == len(reqs) and all(r.done is not None for r in reqs)
+    assert stats["max_inflight"] > 1  # batches overlapped on the device
+    al = dib.Aligner(st, len(w.pairs), k=17)
+    for X in sorted({x for _, x, _ in specs}):
+        whole = al.align(w.pairs, dib.Scoring(1, -1, -1, X))
+        for r, (_, x, idx) in zip(reqs, specs):
+            if x == X:
+                assert r.result.tobytes() == whole[idx].tobytes(), "request %d (X=%d) differs" % (r.rid, X)

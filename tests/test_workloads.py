@@ -123,3 +123,36 @@ def test_seed_options_of_sec5():
         same[g[:-1]] = False  # records after the first of their pair
         assert np.all(pa[1:][same[1:]] - pa[:-1][same[1:]] >= gap)
         assert np.all(w.pairs["seed_id"][same] == w.pairs["seed_id"][np.flatnonzero(same) - 1] + 1)
+
+
+def _restrict(pairs, ranges):
+    m = np.zeros(len(pairs), bool)
+    for lo, hi in ranges:
+        m |= (pairs["read_a"] >= lo) & (pairs["read_a"] < hi)
+    return pairs[m]
+
+
+def test_read_range_index_equals_the_full_index():
+    """pairs_mode PAIRS_RANGES builds only the k-mers of the chosen reads (the
+    way the full-size repeat genome's pairs are checked in read blocks) and must
+    give exactly the full index's records with read_a in those ranges."""
+    for name, over in (("c1_tiny", {}),
+                       ("c4_repeats_small", dict(genome_len=400_000, repeat_families=3, tandem_bases=20_000,
+                                                 max_seeds=3, min_seed_gap=200))):
+        full = workloads.generate(name, **over)
+        n = full.n_reads
+        ranges = [(0, n // 7), (n // 3, n // 3 + n // 10), (n - 5, n + 3)]
+        part = workloads.generate(name, pairs_mode=workloads.PAIRS_RANGES, read_ranges=ranges, cache=False,
+                                  **over)
+        exp = _restrict(full.pairs, ranges)
+        assert len(exp) > 0
+        assert part.reads.tobytes() == full.reads.tobytes()
+        assert part.pairs.tobytes() == exp.tobytes(), name
+        assert part.stats["instances"] == full.stats["instances"]
+
+
+def test_reads_only_mode():
+    full = workloads.generate("c1_tiny")
+    none = workloads.generate("c1_tiny", pairs_mode=workloads.PAIRS_NONE, cache=False)
+    assert none.reads.tobytes() == full.reads.tobytes() and none.offsets.tobytes() == full.offsets.tobytes()
+    assert len(none.pairs) == 0

@@ -58,7 +58,13 @@ class _Config(ctypes.Structure):
         ("p_sub", ctypes.c_double), ("p_ins", ctypes.c_double), ("p_del", ctypes.c_double),
         ("k", ctypes.c_int32), ("mult_lo", ctypes.c_int32), ("mult_hi", ctypes.c_int32),
         ("max_seeds", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("min_seed_gap", ctypes.c_int32),
+        ("pairs_mode", ctypes.c_int32), ("n_ranges", ctypes.c_int64), ("ranges", ctypes.c_void_p),
     ]
+
+# pairs_mode of the generator: every candidate pair, none (reads only), or the
+# candidate pairs whose read_a lies in given read-id ranges (same records as the
+# full index restricted to those read_a, from an index of the ranges' k-mers only).
+PAIRS_ALL, PAIRS_NONE, PAIRS_RANGES = 0, 1, 2
 
 
 _BASE = dict(seed=1, genome_len=50_000, repeat_families=0, repeat_unit_len=5000, repeat_copies=2,
@@ -164,11 +170,22 @@ def _cache_dir() -> str:
     return d
 
 
-def generate(name: str | None = None, *, cache: bool = True, n_threads: int = 0, **overrides) -> Workload:
-    """Generate (or load from the cache) a named configuration, optionally overridden."""
+def generate(name: str | None = None, *, cache: bool = True, n_threads: int = 0, pairs_mode: int = PAIRS_ALL,
+             read_ranges=None, **overrides) -> Workload:
+    """Generate (or load from the cache) a named configuration, optionally overridden.
+
+    pairs_mode PAIRS_NONE skips the candidate pairs (reads only); PAIRS_RANGES
+    keeps the candidate pairs whose read_a lies in one of ``read_ranges``
+    (half-open (lo, hi) read-id ranges, ascending and disjoint)."""
     params = dict(CONFIGS[name] if name else _BASE)
     params.update(overrides)
-    key = hashlib.sha256(repr(sorted(params.items())).encode() + open(_SRC, "rb").read()).hexdigest()[:16]
+    ranges = np.ascontiguousarray(np.asarray(read_ranges if read_ranges is not None else [], dtype=np.int64)
+                                  .reshape(-1, 2))
+    if pairs_mode == PAIRS_RANGES and len(ranges) and (np.any(ranges[:, 1] < ranges[:, 0]) or
+                                                       np.any(ranges[1:, 0] < ranges[:-1, 1])):
+        raise ValueError("read ranges must be ascending and disjoint")
+    key_src = repr(sorted(params.items())) + repr((pairs_mode, ranges.tolist()))
+    key = hashlib.sha256(key_src.encode() + open(_SRC, "rb").read()).hexdigest()[:16]
     path = os.path.join(_cache_dir(), "%s_%s.npz" % (name or "custom", key))
     if cache and os.path.exists(path):
         z = np.load(path)
@@ -176,8 +193,11 @@ def generate(name: str | None = None, *, cache: bool = True, n_threads: int = 0,
                         z["tmpl_len"], z["tmpl_strand"], z["pairs"].view(PAIR_DTYPE).reshape(-1),
                         dict(zip(["instances", "retained_kmers", "candidate_pairs"], z["stats"].tolist())))
     lib = _load()
-    cfg = _Config(**{k: v for k, v in params.items()}, n_threads=n_threads)
+    cfg = _Config(**{k: v for k, v in params.items()}, n_threads=n_threads, pairs_mode=pairs_mode,
+                  n_ranges=len(ranges), ranges=ranges.ctypes.data if len(ranges) else None)
     h = lib.wl_generate(ctypes.byref(cfg))
+    if not h:
+        raise ValueError("the generator rejected its configuration")
     try:
         gl, nr, nb, npairs = lib.wl_genome_len(h), lib.wl_n_reads(h), lib.wl_n_bases(h), lib.wl_n_pairs(h)
         w = Workload(

@@ -67,6 +67,10 @@ typedef struct {
   int32_t max_seeds;
   int32_t n_threads;
   int32_t min_seed_gap;        // least pos_a distance between seeds of a pair (0 = k)
+  int32_t pairs_mode;          // 0 every candidate pair; 1 none (reads only); 2 the candidate
+                               // pairs whose read_a lies in one of the ranges below
+  int64_t n_ranges;            // pairs_mode 2: number of half-open read-id ranges
+  const int64_t* ranges;       // pairs_mode 2: lo0, hi0, lo1, hi1, ... (ascending, disjoint)
 } wl_config_t;
 
 typedef struct {
@@ -283,6 +287,8 @@ struct RawPair {
   uint8_t strand;
 };
 
+void select_seeds(const wl_config_t& c, Workload& w, std::vector<std::vector<RawPair>>& emitted);
+
 void make_pairs(const wl_config_t& c, Workload& w) {
   const int k = c.k;
   const int threads = n_workers(c);
@@ -380,6 +386,16 @@ void make_pairs(const wl_config_t& c, Workload& w) {
   inst.shrink_to_fit();
   for (int q = 0; q < kParts; ++q) w.n_retained_kmers += retained[(size_t)q];
 
+  select_seeds(c, w, emitted);
+}
+
+// Group the occurrence pairs by read pair and apply the seed rule (Sec. 8 seed
+// constraints, Sec. 5 options); appends the records to w.pairs, sorted by
+// (read_a, read_b, seed_id).  Consumes `emitted`.
+void select_seeds(const wl_config_t& c, Workload& w, std::vector<std::vector<RawPair>>& emitted) {
+  const int k = c.k;
+  const int threads = n_workers(c);
+  const int kParts = 1024;
   // Group by read pair: partition pairs by read_a so each group sorts independently.
   std::vector<std::vector<RawPair>> by_a((size_t)kParts);
   for (auto& v : emitted) {
@@ -431,15 +447,141 @@ void make_pairs(const wl_config_t& c, Workload& w) {
   });
 }
 
+// The candidate pairs whose read_a lies in the configured read-id ranges,
+// without indexing every k-mer of the read set: the same pairs and seeds as
+// make_pairs, restricted to those read_a (memory grows with the ranges' k-mers,
+// not with the whole read set; the multiplicities still count every read).
+//   1. the canonical codes of the range reads, sorted and unique (the set S);
+//   2. a 2^32-bit filter of S by hash; every occurrence of every read whose
+//      code passes the filter and is found in S counts towards its code;
+//   3. the occurrences of the retained codes of S (multiplicity in
+//      [mult_lo, mult_hi]) are collected and sorted by (code, read, position);
+//   4. per code, every occurrence pair of distinct reads whose smaller read
+//      lies in a range becomes an occurrence pair; seed selection as before.
+bool in_ranges(const wl_config_t& c, uint32_t r) {
+  for (int64_t q = 0; q < c.n_ranges; ++q)
+    if ((int64_t)r >= c.ranges[2 * q] && (int64_t)r < c.ranges[2 * q + 1]) return true;
+  return false;
+}
+
+template <class F>
+void for_each_kmer(const Workload& w, int64_t r, int k, F&& f) {
+  const uint64_t mask = (k == 32) ? ~0ull : ((1ull << (2 * k)) - 1);
+  const char* s = w.reads.data() + w.offsets[(size_t)r];
+  const int64_t L = w.offsets[(size_t)r + 1] - w.offsets[(size_t)r];
+  uint64_t fw = 0, rc = 0;
+  for (int64_t p = 0; p < L; ++p) {
+    const uint64_t b = (uint64_t)base_code(s[p]);
+    fw = ((fw << 2) | b) & mask;
+    rc = (rc >> 2) | ((3 - b) << (2 * (k - 1)));
+    if (p + 1 >= k) f(std::min(fw, rc), fw <= rc ? 0u : 1u, (uint32_t)(p + 1 - k));
+  }
+}
+
+void make_pairs_ranges(const wl_config_t& c, Workload& w) {
+  const int k = c.k;
+  const int threads = n_workers(c);
+  const int64_t n = (int64_t)w.offsets.size() - 1;
+  std::vector<int64_t> rlist;
+  for (int64_t q = 0; q < c.n_ranges; ++q)
+    for (int64_t r = std::max<int64_t>(0, c.ranges[2 * q]); r < std::min<int64_t>(n, c.ranges[2 * q + 1]); ++r)
+      rlist.push_back(r);
+  // 1. codes of the range reads
+  std::vector<std::vector<uint64_t>> local((size_t)rlist.size());
+  parallel_for((int64_t)rlist.size(), threads, [&](int64_t i) {
+    std::vector<uint64_t>& v = local[(size_t)i];
+    for_each_kmer(w, rlist[(size_t)i], k, [&](uint64_t code, uint32_t, uint32_t) { v.push_back(code); });
+  });
+  std::vector<uint64_t> S;
+  for (auto& v : local) {
+    S.insert(S.end(), v.begin(), v.end());
+    std::vector<uint64_t>().swap(v);
+  }
+  std::sort(S.begin(), S.end());
+  S.erase(std::unique(S.begin(), S.end()), S.end());
+  // 2. filter, then count every occurrence of the codes of S over all reads
+  const int kFilterBits = 32;
+  std::vector<uint64_t> filter((size_t)1 << (kFilterBits - 6), 0);
+  auto fbit = [&](uint64_t code) { return splitmix64(code) >> (64 - kFilterBits); };
+  for (uint64_t code : S) {
+    const uint64_t b = fbit(code);
+    filter[(size_t)(b >> 6)] |= 1ull << (b & 63);
+  }
+  auto find = [&](uint64_t code) -> int64_t {
+    const uint64_t b = fbit(code);
+    if (!((filter[(size_t)(b >> 6)] >> (b & 63)) & 1ull)) return -1;
+    auto it = std::lower_bound(S.begin(), S.end(), code);
+    return (it != S.end() && *it == code) ? (int64_t)(it - S.begin()) : -1;
+  };
+  std::vector<uint32_t> cnt(S.size(), 0);
+  std::atomic<int64_t> total(0);
+  parallel_for(n, threads, [&](int64_t r) {
+    int64_t here = 0;
+    for_each_kmer(w, r, k, [&](uint64_t code, uint32_t, uint32_t) {
+      ++here;
+      const int64_t i = find(code);
+      if (i >= 0) __atomic_fetch_add(&cnt[(size_t)i], 1u, __ATOMIC_RELAXED);
+    });
+    total.fetch_add(here);
+  });
+  w.n_instances = total.load();
+  // 3. occurrences of the retained codes of S
+  auto retained = [&](int64_t i) { return cnt[(size_t)i] >= (uint32_t)c.mult_lo && cnt[(size_t)i] <= (uint32_t)c.mult_hi; };
+  for (size_t i = 0; i < S.size(); ++i) w.n_retained_kmers += retained((int64_t)i) ? 1 : 0;
+  std::vector<std::vector<Instance>> found((size_t)n);
+  parallel_for(n, threads, [&](int64_t r) {
+    for_each_kmer(w, r, k, [&](uint64_t code, uint32_t orient, uint32_t pos) {
+      const int64_t i = find(code);
+      if (i >= 0 && retained(i)) found[(size_t)r].push_back({code, (uint32_t)r, pos | (orient << 31)});
+    });
+  });
+  std::vector<Instance> inst;
+  for (auto& v : found) {
+    inst.insert(inst.end(), v.begin(), v.end());
+    std::vector<Instance>().swap(v);
+  }
+  std::sort(inst.begin(), inst.end(), [](const Instance& x, const Instance& y) {
+    if (x.canon != y.canon) return x.canon < y.canon;
+    if (x.rid != y.rid) return x.rid < y.rid;
+    return x.pos_orient < y.pos_orient;
+  });
+  // 4. occurrence pairs whose smaller read is in a range
+  std::vector<std::vector<RawPair>> emitted(1);
+  for (size_t a = 0; a < inst.size();) {
+    size_t e = a + 1;
+    while (e < inst.size() && inst[e].canon == inst[a].canon) ++e;
+    for (size_t x = a; x < e; ++x) {
+      if (!in_ranges(c, inst[x].rid)) continue;
+      for (size_t y = x + 1; y < e; ++y) {
+        if (inst[x].rid == inst[y].rid) continue;
+        RawPair p;
+        p.ra = inst[x].rid;
+        p.rb = inst[y].rid;
+        p.pa = inst[x].pos_orient & 0x7FFFFFFFu;
+        p.pb = inst[y].pos_orient & 0x7FFFFFFFu;
+        p.strand = (uint8_t)((inst[x].pos_orient >> 31) ^ (inst[y].pos_orient >> 31));
+        emitted[0].push_back(p);
+      }
+    }
+    a = e;
+  }
+  select_seeds(c, w, emitted);
+}
+
 }  // namespace
 
 extern "C" {
 
 void* wl_generate(const wl_config_t* cfg) {
+  if (cfg->pairs_mode < 0 || cfg->pairs_mode > 2) return nullptr;
+  if (cfg->pairs_mode == 2 && (cfg->n_ranges < 0 || (cfg->n_ranges > 0 && !cfg->ranges))) return nullptr;
   Workload* w = new Workload();
   make_genome(*cfg, *w);
   make_reads(*cfg, *w);
-  make_pairs(*cfg, *w);
+  if (cfg->pairs_mode == 0)
+    make_pairs(*cfg, *w);
+  else if (cfg->pairs_mode == 2)
+    make_pairs_ranges(*cfg, *w);
   return w;
 }
 
