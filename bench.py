@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mono", action="store_true", help="skip the score-versus-X violation count")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split the one batch across ranks by cost key (whole candidate pairs) instead of "
+                         "aligning a replica per rank")
     # profiling / exploration knobs (the defaults are the benchmark)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--xdrops", default=",".join(str(x) for x in XDROPS))
@@ -84,6 +88,8 @@ def parse():
     ap.add_argument("--stream-genome", type=int, default=0,
                     help="stream mode: override the genome length (repeat content scaled with it)")
     ap.add_argument("--n-parts", type=int, default=8, help="stream mode: hash passes of the k-mer count")
+    ap.add_argument("--tune-workload", default="c3_uneven", help="tune mode: workload")
+    ap.add_argument("--tune-x", type=int, default=50, help="tune mode: X-drop")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     args = ap.parse_args()
@@ -299,28 +305,35 @@ def _time_direct(torch, al, n, scoring, stream, sched, reps):
 
 def mode_tune(args):
     """Uneven batch (log-uniform 500 bp - 100 kb reads, per-read error 5-35%,
-    X = 50): the library's default schedule against the schedule its autotuner
-    picks on an independent draw of the same workload (generator seed 103), so
-    the tuned schedule is judged on data it was not tuned on.  (A 10% sample of
-    the batch itself misled the tuner: with a tenth of the extensions per warp,
-    the longest extensions dominate its timings.)"""
+    X = 50; or another workload and X): the schedule the autotuner picks on an
+    independent draw of the same workload (generator seed + 100), so the tuned
+    schedule is judged on data it was not tuned on, against the library's
+    default schedule and against a naive fixed one (one length bucket, every
+    extension to the warp-per-extension form).  (A 10% sample of the batch
+    itself misled the tuner: with a tenth of the extensions per warp, the
+    longest extensions dominate its timings.)"""
     import torch
     import paper_2001_10049_gb300 as dib
     dev = torch.device("cuda", 0)
-    w = workloads.generate("c3_uneven")
+    wname = args.tune_workload
+    w = workloads.generate(wname)
     pairs = w.pairs
     n = len(pairs)
-    X = 50
+    X = args.tune_x
     store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
     al = dib.Aligner(store, n, k=K, device=dev)
     al.upload_pairs(pairs)
     stream = torch.cuda.Stream(device=dev)
     sc = dib.Scoring(1, -1, -1, X)
     fixed = dib.dibella_get_default_schedule()
+    naive_d = fixed.as_dict()
+    naive_d.update(narrow_max_xdrop=-1, n_buckets=1, bucket_bounds=[], mid_band_cap=0)
+    naive = dib.Schedule.from_dict(naive_d)
     with ClockSampler(0) as clocks:
         fixed_ms = _time_direct(torch, al, n, sc, stream, fixed, args.steps)
         c_fixed = dib.dibella_batch_counters(al.workspace, stream=stream)
-        tw = workloads.generate("c3_uneven", seed=103)
+        naive_ms = _time_direct(torch, al, n, sc, stream, naive, args.steps)
+        tw = workloads.generate(wname, seed=workloads.CONFIGS[wname]["seed"] + 100)
         tstore = dib.ReadStore.from_ascii(tw.reads, tw.offsets, device=dev)
         tal = dib.Aligner(tstore, len(tw.pairs), k=K, device=dev)
         tal.upload_pairs(tw.pairs)
@@ -338,7 +351,7 @@ def mode_tune(args):
     print(json.dumps({
         "metric": "aligned pairs/s", "mode": "tune", "cpu_baseline": cpu, "unit": "aligned pairs/s", "n_gpus": 1,
         "value": n_cand / (tuned_ms * 1e-3), "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "c3_uneven", "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n,
+        "config": {"workload": wname, "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n,
                    "extensions": 2 * n, "xdrop": X, "scoring": "+1/-1/-1", "k": K, "steps": args.steps,
                    "l2": "flushed (256 MiB write) before every timed batch"},
         "fixed": {"schedule": fixed.as_dict(), "ms": fixed_ms, "pairs_per_s": n_cand / (fixed_ms * 1e-3),
@@ -346,9 +359,13 @@ def mode_tune(args):
         "tuned": {"schedule": best.as_dict(), "ms": tuned_ms, "pairs_per_s": n_cand / (tuned_ms * 1e-3),
                   "gcups": cells / (tuned_ms * 1e-3) / 1e9, "counters": c_tuned, "tuning_batch_ms": best_ms,
                   "schedules_tried": tried, "tuning_s": tune_s,
-                  "tuned_on": "an independent draw of c3_uneven (generator seed 103): %d candidate pairs, "
-                              "%d seed records" % (len(workloads.pair_groups(tw.pairs)) - 1, len(tw.pairs))},
+                  "tuned_on": "an independent draw of %s (generator seed %d): %d candidate pairs, "
+                              "%d seed records" % (wname, workloads.CONFIGS[wname]["seed"] + 100,
+                                                   len(workloads.pair_groups(tw.pairs)) - 1, len(tw.pairs))},
+        "naive": {"schedule": naive.as_dict(), "ms": naive_ms, "pairs_per_s": n_cand / (naive_ms * 1e-3)},
         "speedup_tuned_vs_fixed": fixed_ms / tuned_ms,
+        "speedup_tuned_vs_naive": naive_ms / tuned_ms,
+        "speedup_fixed_vs_naive": naive_ms / fixed_ms,
         "clocks": clocks.summary(),
     }))
 
@@ -686,6 +703,13 @@ def main():
     pairs = w.pairs
     if args.sample_pairs:
         pairs = workloads.sample_pair_groups(pairs, args.sample_pairs, seed=29)
+    n_cand_total = len(workloads.pair_groups(pairs)) - 1
+    shard_info = None
+    if args.shard and world > 1:
+        from paper_2001_10049_gb300 import shard
+        shares, totals = shard.partition(pairs, w.read_lengths, K, world)
+        pairs = pairs[shares[rank]]
+        shard_info = {"cost_keys": [int(t) for t in totals], "max_over_mean": float(totals.max() / totals.mean())}
     n_seeds = len(pairs)
     sched = None
     if args.schedule:
@@ -754,6 +778,47 @@ def main():
     torch.cuda.synchronize(dev)
     assert al.results_host(n_seeds).tobytes() == res_graph.tobytes(), "graph replay differs from direct call"
 
+    # Score against X (outside the timed region): X-drop's best is not monotone
+    # in X (a larger X can raise the best early and prune a path that a smaller
+    # X keeps), so violations are counted, not asserted, over X in {7, 25, 50}.
+    mono = None
+    if not args.no_mono:
+        mono_x = (7, 25, 50)
+        scores = {}
+        for X in mono_x:
+            al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
+            torch.cuda.synchronize(dev)
+            r = al.results_host(n_seeds)
+            scores[X] = r["score"].astype(np.int64)
+            valid = (r["status"] & 2) == 0
+        mono = {"xdrops": list(mono_x), "seed_records": int(valid.sum())}
+        for a, b in ((7, 25), (25, 50), (7, 50)):
+            v = valid & (scores[a] > scores[b])
+            mono["violations_%d_%d" % (a, b)] = int(v.sum())
+            mono["max_drop_%d_%d" % (a, b)] = int((scores[a] - scores[b])[v].max()) if v.any() else 0
+
+    # Load balance of the persistent queues (outside the timed region): one more
+    # batch per X with the per-warp clock on each launch, each warp's finish
+    # time measured from the launch's first warp start (the analogue of the
+    # paper's max/avg rank time, Sec. 9 and Fig. 8).
+    balance = {}
+    for X in XD:
+        balance[str(X)] = {}
+        for name, which in dib.WARP_CLOCK_LAUNCHES.items():
+            dib.dibella_enable_warp_clock(which)
+            al.run(n_seeds, (1, -1, -1, X), stream=stream, sched=sched)
+            torch.cuda.synchronize(dev)
+            wc = dib.dibella_warp_clock()
+            dib.dibella_enable_warp_clock(0)
+            if len(wc) == 0 or wc[:, 1].max() == 0:
+                continue
+            wc = wc[wc[:, 1] > 0].astype(np.int64)
+            fin = wc[:, 1] - wc[:, 0].min()
+            balance[str(X)][name] = {"warps": int(len(wc)), "span_ms": float(fin.max() / 1e6),
+                                     "mean_finish_ms": float(fin.mean() / 1e6),
+                                     "max_over_mean": float(fin.max() / max(fin.mean(), 1.0)),
+                                     "p50_finish_ms": float(np.percentile(fin, 50) / 1e6)}
+
     # End to end through the host-buffer entry point (H2D pairs, D2H results timed).
     host_pairs = torch.from_numpy(pairs.view(np.uint8).reshape(-1, 24).copy()).pin_memory()
     host_res = torch.empty((n_seeds, 40), dtype=torch.uint8).pin_memory()
@@ -787,7 +852,7 @@ def main():
         dt = time.perf_counter() - t0
         plain = {"value": len(XD) * n_cand_s / dt, "unit": "aligned pairs/s",
                  "sample": "%d candidate pairs (%d seed records, seed 23), X=%s, one kernel launch "
-                           "(one warp) per seed on one stream, no graph"
+                           "(one warp, packed register form) per candidate pair on one stream, no graph"
                            % (n_cand_s, len(sample), ",".join(map(str, XD)))}
 
     cpu = None
@@ -824,7 +889,7 @@ def main():
     int_peaks, int_clk = measured_int_peaks(dib, stream, local)
     cell_peak = int_peaks[dib.INT_PEAK_CLASSES[4]]["tops"]
     total_cells = sum(cells.values())
-    value = world * len(XD) * n_cand / (my_ms * 1e-3)
+    value = (len(XD) * n_cand_total if shard_info else world * len(XD) * n_cand) / (my_ms * 1e-3)
     out = {
         "metric": "aligned pairs/s",
         "value": value,
@@ -834,7 +899,7 @@ def main():
         "warmup": args.warmup,
         "ms_per_step": my_ms,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if shard_info else "weak",
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
@@ -845,7 +910,9 @@ def main():
                    "schedule": (sched or dib.dibella_get_default_schedule()).as_dict(),
                    "l2": "flushed (256 MiB write) before every timed batch",
                    "graph": "one CUDA graph per X (whole dibella_xdrop_batch)",
-                   "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+                   "parallelism": ("cost-balanced shard of one batch" if shard_info else "replica per GPU")
+                                  if world > 1 else "1 GPU",
+                   "shard": shard_info},
         "gcups": total_cells / (my_ms * 1e-3) / 1e9,
         "per_xdrop": {str(X): {"ms": batch_ms[X], "pairs_per_s": n_cand / (batch_ms[X] * 1e-3),
                                "gcups": cells[X] / (batch_ms[X] * 1e-3) / 1e9, "cells": cells[X],
@@ -865,13 +932,16 @@ def main():
                      "peak_measured_class": "int32 DP cell, 8 ops (compare, select, add; max, add; max; "
                                             "compare, select), full grid of independent chains",
                      "int_peaks_measured": int_peaks, "int_peaks_clocks": int_clk},
-        "e2e": ({"value": world * len(XD) * n_cand / (e2e_step * 1e-3), "unit": "aligned pairs/s",
+        "e2e": ({"value": (len(XD) * n_cand_total if shard_info else world * len(XD) * n_cand) / (e2e_step * 1e-3),
+                 "unit": "aligned pairs/s",
                  "h2d_bytes_per_step": len(XD) * n_seeds * 24, "d2h_bytes_per_step": len(XD) * n_seeds * 40}
                 if e2e_step else None),
         "gpu_launches": args.steps * sum(launches[X] for X in XD),
         "clocks": clk,
         "plain_per_pair": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
+        "score_vs_x": mono,
+        "queue_balance": balance,
         "cpu_baseline": cpu,
     }
     print(json.dumps(out))

@@ -279,10 +279,13 @@ int dibella_xdrop_stream(const uint32_t* packed_words, const int64_t* read_word_
                          int64_t workspace_bytes, void* const* streams, const dibella_schedule_t* sched,
                          int64_t* n_chunks_out);
 
-/* Baseline form of the same computation: one kernel launch per seed (one
- * warp, left then right extension, no queues, no graph), all on `stream`.
+/* Baseline form of the same computation: one kernel launch per candidate
+ * pair (one warp runs the left then the right extension of each of the
+ * pair's seed records, with the batched path's packed register form and its
+ * escalations; no queues, no persistent kernels, no graph), all on `stream`.
  * Same arguments and results as dibella_xdrop_batch; used to measure what
- * batching buys.  Requires the same workspace. */
+ * batching buys.  Requires the same workspace.  Reads the records back to
+ * the host once (a synchronisation) to find the candidate pairs. */
 int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_word_offsets,
                            const int32_t* read_lengths, int64_t n_reads,
                            const dibella_pair_t* pairs, int64_t n_pairs, int32_t k,
@@ -472,6 +475,20 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
  * queue is empty) and combine.  Host-side count; no device work, no errors.
  * The paper has no counterpart: it reports the GPU work of a batch. */
 int dibella_last_launch_count(void);
+
+/* Per-warp clock of one extension launch, for the load balance of the
+ * persistent queues (the paper measures the same imbalance as max/avg time
+ * over ranks, Sec. 9): after dibella_enable_warp_clock(launch) with launch =
+ * 1 narrow form, 2 first wide launch, 3 mid form, 4 wide launch on the
+ * escalations (0 = off), every later batch has each warp of that launch write
+ * the GPU's global timer (ns) when it starts and when it finds its queue
+ * empty and leaves.  dibella_warp_clock synchronises the device and copies
+ * the last clocked launch's (start, end) pairs, 2 x uint64 per warp, for at
+ * most max_warps warps (65536 at most are clocked); returns the number of
+ * warps written, or a negative status.  One clock array serves the process:
+ * clock one batch at a time.  The paper has no counterpart: a measurement. */
+int dibella_enable_warp_clock(int launch);
+int dibella_warp_clock(uint64_t* out, int max_warps);
 
 /* Measured integer throughput of one instruction class, the ceiling the
  * extension kernels' cell rates are compared with: every thread of a grid

@@ -118,6 +118,8 @@ def _lib():
             "dibella_phase_times": ([ctypes.POINTER(ctypes.c_float), ctypes.c_int], i32),
             "dibella_batch_counters": ([vp, vp, p64, ctypes.c_int], i32),
             "dibella_last_launch_count": ([], i32),
+            "dibella_enable_warp_clock": ([ctypes.c_int], i32),
+            "dibella_warp_clock": ([vp, ctypes.c_int], i32),
             "dibella_int_peak": ([i32, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp],
                                  i32),
             "dibella_candidate_workspace_bytes": ([i64, i64, i32, i32, p64], i32),
@@ -382,6 +384,23 @@ def dibella_batch_counters(workspace, stream=None) -> dict:
             "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder",
             "cells_mid", "escalated_mid"]
     return {keys[i]: int(buf[i]) for i in range(n)}
+
+
+WARP_CLOCK_LAUNCHES = {"narrow form": 1, "wide form, first launch": 2, "mid form on the narrow escalations": 3,
+                       "wide form on the escalations": 4}
+
+
+def dibella_enable_warp_clock(launch: int) -> None:
+    _check(_lib().dibella_enable_warp_clock(launch), "dibella_enable_warp_clock")
+
+
+def dibella_warp_clock(max_warps: int = 1 << 16) -> np.ndarray:
+    """(start, end) global-timer ns of every warp of the last clocked launch."""
+    buf = np.zeros((max_warps, 2), dtype=np.uint64)
+    n = _lib().dibella_warp_clock(buf.ctypes.data, max_warps)
+    if n < 0:
+        _check(n, "dibella_warp_clock")
+    return buf[:n]
 
 
 INT_PEAK_CLASSES = {0: "IADD", 1: "IMNMX", 2: "VIADDMNMX int16x2", 3: "VIMNMX3 int16x2",

@@ -112,6 +112,9 @@ struct ExtendParams {
   int cells_idx;  // Counters::cells entry the wide forms add to
   int narrow_cells_idx;  // Counters::cells entry of the one-lane forms (0 narrow, 6 mid)
   int narrow_esc_stat;   // Counters::stat entry counting their escalations (2 narrow, 6 mid)
+  // Per-warp clock of one launch (null unless requested): warp w writes the
+  // global timer (ns) when it starts, at [2w], and when it leaves, at [2w+1].
+  unsigned long long* wclock;
   Scoring sc;
   int* gband;
   int gcap;
@@ -126,6 +129,24 @@ __device__ __forceinline__ uint32_t base_window(const uint32_t* __restrict__ wor
 
 __device__ __forceinline__ int base_at(const uint32_t* __restrict__ words, long long idx) {
   return (int)((__ldg(words + (idx >> 4)) >> ((unsigned)(idx & 15) * 2u)) & 3u);
+}
+
+constexpr int kMaxClockedWarps = 1 << 16;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Start and end of this warp's work in a clocked launch (lane 0 writes).
+__device__ __forceinline__ void warp_clock_out(unsigned long long* wclock, unsigned long long t0) {
+  if (wclock == nullptr || (threadIdx.x & 31) != 0) return;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w < kMaxClockedWarps) {
+    wclock[2 * w] = t0;
+    wclock[2 * w + 1] = global_ns();
+  }
 }
 
 __device__ __forceinline__ unsigned pop_warp(Counters* cnt, int q) {
@@ -800,6 +821,7 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
 template <int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
+  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const bool fwd = tail <= p.forward_max;
   for (;;) {
@@ -823,6 +845,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
     }
     __syncwarp();
   }
+  warp_clock_out(p.wclock, wt0);
 }
 
 // Packed form, one warp per extension (routed here only when X <= kPackedMaxX).
@@ -834,6 +857,7 @@ template <int NC>
 __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (NC == 24 ? 4 : 1)))
     wide_pk_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
+  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const bool fwd = NC > 8 && tail <= p.forward_max;  // 8 slots is never a ladder rung
   for (;;) {
@@ -857,6 +881,7 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
     }
     __syncwarp();
   }
+  warp_clock_out(p.wclock, wt0);
 }
 
 // Grouped packed form: a warp runs NG = 32/GL extensions at once, GL lanes
@@ -894,6 +919,7 @@ __device__ __forceinline__ int grp_reduce_min(int v, int g) {
 template <int GL, int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p) {
   static_assert(GL == 8 || GL == 16, "group of 8 or 16 lanes");
+  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
   static_assert(NC % 8 == 0 && NC >= 8 && NC <= 32, "slots come in words of 8");
   constexpr int NW = NC / 8;
   constexpr int NG = 32 / GL;
@@ -979,7 +1005,10 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
       }
     }
     if (!__any_sync(kFull, active)) {
-      if (__all_sync(kFull, exhausted)) break;
+      if (__all_sync(kFull, exhausted)) {
+        warp_clock_out(p.wclock, wt0);
+        break;
+      }
       continue;
     }
 
@@ -1386,6 +1415,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
   extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
   T* wbase = reinterpret_cast<T*>(smem_words) + (threadIdx.x >> 5) * (2 * WT * 32);
+  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
   const unsigned ntail = *((volatile unsigned*)&p.cnt->tail[p.narrow_q_id]);
   NarrowLane<WT> L;
   bool active = false, exhausted = false;
@@ -1415,7 +1445,10 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
       }
     }
     if (!__any_sync(kFull, active)) {
-      if (__all_sync(kFull, exhausted)) break;
+      if (__all_sync(kFull, exhausted)) {
+        warp_clock_out(p.wclock, wt0);
+        break;
+      }
       continue;
     }
     if (active) {
@@ -1638,26 +1671,34 @@ __global__ void best_of_pair_kernel(const dibella_pair_t* __restrict__ pairs, lo
   }
 }
 
-// One launch per seed (baseline form): one warp aligns the left then the right
-// extension of seed `t`, band in shared memory (1024 cells) or, if it
-// outgrows that, in the workspace band slot 0.
+// One launch per candidate pair (the baseline form): one warp aligns, seed by
+// seed, the left then the right extension of every seed record in [t0, t1)
+// with the same per-extension code as the batched path: the packed register
+// form with 8 slots (int32 register form above X = kPackedMaxX), then 32 slots
+// when its band outgrows that, then the band in workspace slot 0.  No queues,
+// no persistence, no graph: what batching adds is measured against this.
 __global__ void __launch_bounds__(32) per_pair_kernel(const uint32_t* __restrict__ words,
-                                                      const Item* __restrict__ items, ExtOut* ext,
-                                                      long long t, Scoring sc, int* gband, int gcap) {
-  __shared__ int arr[3 * 1024];
-  for (int s = 0; s < 2; ++s) {
-    const Item it = items[2 * t + s];
-    if (it.tag < 0) continue;
-    if (!extend_warp<false>(words, it, sc, arr, 1024, ext + 2 * t + s)) {
-      if (!extend_warp<true>(words, it, sc, gband, gcap, ext + 2 * t + s)) {
+                                                      const Item* __restrict__ items, ExtOut* ext, long long t0,
+                                                      long long t1, Scoring sc, int* gband, int gcap) {
+  for (long long t = t0; t < t1; ++t)
+    for (int s = 0; s < 2; ++s) {
+      const Item it = items[2 * t + s];
+      if (it.tag < 0) continue;
+      ExtOut* o = ext + 2 * t + s;
+      bool ok;
+      if (sc.X <= kPackedMaxX)
+        ok = extend_pk<8>(words, it, sc, o) || extend_pk<32>(words, it, sc, o);
+      else
+        ok = extend_reg<32>(words, it, sc, o);
+      if (!ok && !extend_warp<true>(words, it, sc, gband, gcap, o)) {
         if (threadIdx.x == 0) {
-          ExtOut o;
-          o.best = 0; o.i_end = 0; o.j_end = 0; o.status = DIBELLA_RES_BAND_OVERFLOW; o.cells = 0;
-          ext[2 * t + s] = o;
+          ExtOut b;
+          b.best = 0; b.i_end = 0; b.j_end = 0; b.status = DIBELLA_RES_BAND_OVERFLOW; b.cells = 0;
+          *o = b;
         }
       }
+      __syncwarp();
     }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1688,6 +1729,24 @@ DeviceInfo g_dev[64];
 
 bool g_timing = false;
 cudaEvent_t g_ev[8] = {};
+// Per-warp clock of one launch per batch (dibella_enable_warp_clock): which
+// launch (0 none, 1 narrow, 2 first wide, 3 mid, 4 wide on the escalations)
+// and how many warps the last clocked launch ran.
+__device__ unsigned long long g_warp_clock[2 * kMaxClockedWarps];
+int g_clock_launch = 0;
+int g_clocked_warps = 0;
+
+// The clock array for launch `which` of this batch, cleared on `st`; null when
+// that launch is not clocked.
+unsigned long long* clock_for(int which, int warps, cudaStream_t st) {
+  if (g_clock_launch != which) return nullptr;
+  unsigned long long* p = nullptr;
+  if (cudaGetSymbolAddress((void**)&p, g_warp_clock) != cudaSuccess) return nullptr;
+  const int n = std::min(warps, kMaxClockedWarps);
+  if (cudaMemsetAsync(p, 0, sizeof(unsigned long long) * 2 * (size_t)n, st) != cudaSuccess) return nullptr;
+  g_clocked_warps = n;
+  return p;
+}
 thread_local int g_launches = 0;  // kernel launches of this thread's last batch
 int g_ev_count = 0;
 
@@ -1884,6 +1943,30 @@ cudaError_t launch_mid(const DeviceInfo& D, int wt, cudaStream_t st, const Exten
   return cudaGetLastError();
 }
 
+// Resident blocks per SM of the wide form launch_wide would run.
+int wide_blocks(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop) {
+  dibella_schedule_t sch = sch_in;
+  const bool packed = sch.wide_packed && xdrop <= kPackedMaxX;
+  int lanes = sch.wide_group_lanes;
+  if (lanes == 0) lanes = 32;
+  if (!packed) lanes = 32;
+  if (sch.wide_slots == 0) sch.wide_slots = (lanes == 32 && packed) ? (xdrop <= 30 ? 8 : 24) : (xdrop <= 30 ? 16 : 24);
+  if (lanes == 8 && sch.wide_slots == 32) sch.wide_slots = 24;
+  if (sch.wide_slots == 8 && (lanes != 32 || !packed)) sch.wide_slots = 16;
+  const int vi = sch.wide_slots == 8 ? 3 : (sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2));
+  int b;
+  if (!packed)
+    b = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
+  else if (lanes == 32)
+    b = D.pk_blocks[vi];
+  else if (lanes == 16)
+    b = D.grp16_blocks[vi];
+  else
+    b = D.grp8_blocks[vi];
+  if (sch.wide_blocks_per_sm > 0) b = std::min(b, sch.wide_blocks_per_sm);
+  return b;
+}
+
 // The wide form of a schedule: packed int16 pairs when allowed, else int32.
 cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, cudaStream_t st,
                         const ExtendParams& ep) {
@@ -1981,7 +2064,9 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.esc_q_id = kQEsc1;
   ep.narrow_cells_idx = 0;
   ep.narrow_esc_stat = 2;
+  ep.wclock = clock_for(1, D.sms * nb * kWarpsPerBlock, st);
   if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
+  ep.wclock = nullptr;
   record(st, 2);
 
   // The configured wide form; its escalations climb the ladder.
@@ -1992,7 +2077,9 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wide_q = q[kQWide];
   ep.wide_q_id = kQWide;
   ep.cells_idx = 1;
+  ep.wclock = clock_for(2, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
+  ep.wclock = nullptr;
   record(st, 3);
   int esc_in = kQEsc1;
   if (sch.mid_band_cap > 0 && narrow_kind(xdrop) == 1) {
@@ -2003,7 +2090,10 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     ep.esc_q_id = kQEsc2;
     ep.narrow_cells_idx = 6;
     ep.narrow_esc_stat = 6;
+    const int mvi = sch.mid_band_cap == 128 ? 0 : (sch.mid_band_cap == 192 ? 1 : 2);
+    ep.wclock = clock_for(3, D.sms * D.mid_blocks[mvi], st);
     if ((e = launch_mid(D, sch.mid_band_cap, st, ep)) != cudaSuccess) return cuda_fail(e, "mid launch");
+    ep.wclock = nullptr;
     ep.narrow_q = nullptr;
     ep.esc_q = q[wide_esc_q];
     ep.esc_q_id = wide_esc_q;
@@ -2013,7 +2103,9 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wide_q = q[esc_in];
   ep.wide_q_id = esc_in;
   ep.cells_idx = 4;
+  ep.wclock = clock_for(4, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
+  ep.wclock = nullptr;
   record(st, 5);
   ep.cells_idx = 5;
   for (int r = 0; r < n_rungs; ++r) {
@@ -2222,6 +2314,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.gcap = gcap;
   ep.forward_max = 0;
   ep.cells_idx = 1;
+  ep.wclock = nullptr;
   int* q[kNumQ];
   for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
@@ -2357,11 +2450,21 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
                         scoring, results, ws, L, sch, st);
   if (rc != DIBELLA_OK) return rc;
   const Scoring sc = {scoring.match, scoring.mismatch, scoring.gap, scoring.xdrop};
-  for (long long t = 0; t < n_pairs; ++t) {
-    per_pair_kernel<<<1, 32, 0, st>>>(packed_words, (const Item*)(ws + L.items), (ExtOut*)(ws + L.ext), t,
+  // The candidate pairs' boundaries (runs of equal read_a, read_b) come from
+  // a host copy of the records, read once before the launches.
+  std::vector<dibella_pair_t> hp((size_t)n_pairs);
+  cudaError_t e = cudaMemcpyAsync(hp.data(), pairs, sizeof(dibella_pair_t) * (size_t)n_pairs,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "per-pair record copy");
+  for (long long t0 = 0; t0 < n_pairs;) {
+    long long t1 = t0 + 1;
+    while (t1 < n_pairs && hp[t1].read_a == hp[t0].read_a && hp[t1].read_b == hp[t0].read_b) ++t1;
+    per_pair_kernel<<<1, 32, 0, st>>>(packed_words, (const Item*)(ws + L.items), (ExtOut*)(ws + L.ext), t0, t1,
                                       sc, (int*)(ws + L.gband), gcap);
+    t0 = t1;
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "per-pair launch");
   return finish(read_lengths, pairs, n_pairs, k, results, (const ExtOut*)(ws + L.ext), st);
 }
@@ -2528,6 +2631,23 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
 }
 
 int dibella_last_launch_count(void) { return g_launches; }
+
+int dibella_enable_warp_clock(int launch) {
+  if (launch < 0 || launch > 4) return DIBELLA_EINVAL;
+  g_clock_launch = launch;
+  g_clocked_warps = 0;
+  return DIBELLA_OK;
+}
+
+int dibella_warp_clock(uint64_t* out, int max_warps) {
+  if (!out || max_warps < 0) return DIBELLA_EINVAL;
+  const int n = std::min(max_warps, g_clocked_warps);
+  if (n == 0) return 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, g_warp_clock, sizeof(unsigned long long) * 2 * (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e, "warp clock read");
+  return n;
+}
 
 const char* dibella_last_error(void) { return g_last_error.c_str(); }
 

@@ -76,7 +76,7 @@ def test_c4_full_size():
     report.update(reads=int(n), bases=int(len(w.reads)), t_generate=round(time.time() - t_all, 1))
     # Parity blocks: two full blocks (sized for >= 4M records each at this
     # workload's pair density) and a seeded 5% of the 2,000-read blocks.
-    full = [(0, 1100), (n // 2, n // 2 + 2300)]
+    full = [(0, 1300), (n // 2, n // 2 + 2600)]
     B = 2000
     rng = np.random.default_rng(20240)
     cand = [b for b in range(n // B) if not any(lo < (b + 1) * B and b * B < hi for lo, hi in full)]

@@ -138,3 +138,18 @@ def test_serving_c5_shaped_requests_match_whole_batches():
         for r, (_, x, idx) in zip(reqs, specs):
             if x == X:
                 assert r.result.tobytes() == whole[idx].tobytes(), "request %d (X=%d) differs" % (r.rid, X)
+
+
+def test_warp_clock_of_a_launch(c1, store):
+    """The per-warp clock of one launch: every warp of the clocked launch
+    reports a start and an end, in order; other launches are not clocked."""
+    import paper_2001_10049_gb300 as dib
+    al = dib.Aligner(store, len(c1.pairs), k=17)
+    dib.dibella_enable_warp_clock(1)  # the narrow form
+    try:
+        ref = al.align(c1.pairs, dib.Scoring(1, -1, -1, 7))
+        wc = dib.dibella_warp_clock()
+    finally:
+        dib.dibella_enable_warp_clock(0)
+    assert len(wc) > 0 and np.all(wc[:, 1] >= wc[:, 0]) and np.all(wc[:, 0] > 0)
+    assert al.align(c1.pairs, dib.Scoring(1, -1, -1, 7)).tobytes() == ref.tobytes()  # clocking changes nothing
