@@ -505,6 +505,17 @@ int dibella_warp_clock(uint64_t* out, int max_warps);
  * The paper has no counterpart: this is measurement infrastructure. */
 int dibella_int_peak(int32_t op_class, int64_t iters, double* ops_per_s_out, double* ms_out, void* stream);
 
+/* Bounds record of the debug build (libdibella_debug.so, compiled with
+ * DIBELLA_BOUNDS_CHECK): its X-drop kernels check every packed-store word
+ * they read, every per-thread shared-memory slot, queue push, item index and
+ * global-band slot; a failed check is recorded (the first one's code, index
+ * and limit, and a count) and the access skipped, never trapped.  Writes
+ * out[0..3] = code (0 = clean; 1 shared slot, 2 queue push, 3 item index,
+ * 4 store word, 5 global band slot), index, limit, count; clears the record
+ * when reset != 0.  Synchronises the device.  Returns 1 in the debug build,
+ * 0 (and zeros) in the release build, or a negative status. */
+int dibella_bounds_check(int64_t* out, int reset);
+
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char* dibella_last_error(void);
 /* Library version string. */

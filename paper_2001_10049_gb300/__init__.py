@@ -86,13 +86,19 @@ class Schedule(ctypes.Structure):
 _LIB = None
 
 
+def debug_build() -> bool:
+    """True when DIBELLA_LIB_VARIANT=debug selects the bounds-checked library."""
+    return os.environ.get("DIBELLA_LIB_VARIANT", "") == "debug"
+
+
 def _lib():
-    """Load libdibella.so (compiling it first if its sources are newer)."""
+    """Load libdibella.so, or libdibella_debug.so when DIBELLA_LIB_VARIANT=debug
+    (compiling it first if its sources are newer)."""
     global _LIB
     if _LIB is None:
-        path = _build.LIB
+        path = _build.lib_path(debug_build())
         if not os.path.exists(path) or _build._stale(path, _build.SOURCES + _build.HEADERS):
-            _build.build()
+            _build.build(debug=debug_build())
         lib = ctypes.CDLL(path)
         vp, i64, i32, p64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)
         sig = {
@@ -131,6 +137,7 @@ def _lib():
             "dibella_traceback_workspace_bytes": ([i64, i32, i64, p64], i32),
             "dibella_xdrop_traceback": ([vp, vp, vp, i64, i32, vp, i64, i32, Scoring, vp, vp, i32, vp, i64, i64,
                                          vp, i64, vp], i32),
+            "dibella_bounds_check": ([p64, ctypes.c_int], i32),
             "dibella_last_error": ([], ctypes.c_char_p),
             "dibella_version": ([], ctypes.c_char_p),
         }
@@ -143,7 +150,16 @@ def _lib():
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(debug_build())
+
+
+def dibella_bounds_check(reset: bool = False):
+    """(is_debug_build, {code, index, limit, count}) of the kernels' bounds record."""
+    buf = (ctypes.c_int64 * 4)()
+    rc = _lib().dibella_bounds_check(buf, 1 if reset else 0)
+    if rc < 0:
+        _check(rc, "dibella_bounds_check")
+    return rc == 1, dict(zip(("code", "index", "limit", "count"), (int(v) for v in buf)))
 
 
 def exported_symbols() -> list[str]:

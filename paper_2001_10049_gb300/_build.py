@@ -11,6 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdibella.so")
+# The same library with every kernel bounds check compiled in (DIBELLA_BOUNDS_CHECK).
+LIB_DEBUG = os.path.join(HERE, "libdibella_debug.so")
 SOURCES = [os.path.join(CSRC, "dibella_xdrop.cu"), os.path.join(CSRC, "dibella_kmers.cu"),
            os.path.join(CSRC, "dibella_traceback.cu"), os.path.join(CSRC, "dibella_peak.cu"),
            os.path.join(CSRC, "dibella_pack.cpp")]
@@ -33,16 +35,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit in parallel and link libdibella.so."""
+def lib_path(debug: bool = False) -> str:
+    return LIB_DEBUG if debug else LIB
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every translation unit in parallel and link libdibella.so (or,
+    with debug, libdibella_debug.so with the kernels' bounds checks)."""
+    target = lib_path(debug)
     with _lock:
-        if not force and not _stale(LIB, SOURCES + HEADERS + [__file__]):
-            return LIB
+        if not force and not _stale(target, SOURCES + HEADERS + [__file__]):
+            return target
         objs, procs = [], []
         for src in SOURCES:
-            obj = os.path.join(CSRC, os.path.basename(src) + ".o")
+            obj = os.path.join(CSRC, os.path.basename(src) + (".dbg.o" if debug else ".o"))
             cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-Xcompiler", "-pthread", "-I", INCLUDE, "-c", src, "-o", obj]
+            if debug:
+                cmd.insert(1, "-DDIBELLA_BOUNDS_CHECK")
             if src.endswith(".cu"):
                 cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
             procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT))
@@ -53,9 +63,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed on %s:\n%s" % (src, out.decode(errors="replace")))
             if verbose and out:
                 print(out.decode(errors="replace"))
-        tmp = LIB + ".tmp%d" % os.getpid()
+        tmp = target + ".tmp%d" % os.getpid()
         subprocess.check_call([_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"])
-        os.replace(tmp, LIB)
+        os.replace(tmp, target)
         for o in objs:
             os.remove(o)
-    return LIB
+    return target

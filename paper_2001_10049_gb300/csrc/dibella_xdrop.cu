@@ -115,20 +115,55 @@ struct ExtendParams {
   // Per-warp clock of one launch (null unless requested): warp w writes the
   // global timer (ns) when it starts, at [2w], and when it leaves, at [2w+1].
   unsigned long long* wclock;
+  long long q_cap;  // entries of every queue and of items / ext (2 x seed records)
   Scoring sc;
   int* gband;
   int gcap;
 };
 
+// ---- bounds checks of the debug build ---------------------------------------
+// Built with -DDIBELLA_BOUNDS_CHECK (libdibella_debug.so), every store word
+// read, per-lane shared-memory slot, queue push, item index and global band
+// slot is checked; a failed check records (code, index, limit) of the first
+// fault and a count in g_bounds_fault and the access is skipped (store reads
+// give 0, slots fall back to slot 0, pushes and items are dropped), so the
+// kernel finishes and the host reads the record (dibella_bounds_check).  No
+// trap.  Codes: 1 narrow slot, 2 queue push, 3 item index, 4 store word,
+// 5 global band slot.  In the release build the checks compile to nothing.
+#ifdef DIBELLA_BOUNDS_CHECK
+__device__ unsigned long long g_bounds_fault[4];
+__device__ long long g_store_words;  // words of the batch's store, set by store_extent_kernel
+__device__ __noinline__ bool bounds_fault(int code, long long v, long long lim) {
+  if (atomicCAS(&g_bounds_fault[0], 0ull, (unsigned long long)code) == 0ull) {
+    g_bounds_fault[1] = (unsigned long long)v;
+    g_bounds_fault[2] = (unsigned long long)lim;
+  }
+  atomicAdd(&g_bounds_fault[3], 1ull);
+  return false;
+}
+#define DIBELLA_IN_BOUNDS(v, lim, code) \
+  ((unsigned long long)(long long)(v) < (unsigned long long)(long long)(lim) ? true \
+                                                                            : bounds_fault((code), (long long)(v), (long long)(lim)))
+#define DIBELLA_STORE_WORDS g_store_words
+#else
+#define DIBELLA_IN_BOUNDS(v, lim, code) true
+#define DIBELLA_STORE_WORDS 0
+#endif
+
+// One word of the packed store (checked in the debug build).
+__device__ __forceinline__ uint32_t ldg_word(const uint32_t* __restrict__ words, long long w) {
+  return DIBELLA_IN_BOUNDS(w, DIBELLA_STORE_WORDS, 4) ? __ldg(words + w) : 0u;
+}
+
 __device__ __forceinline__ uint32_t base_window(const uint32_t* __restrict__ words, long long idx) {
   // 16 bases starting at base index idx (>= 0), base t at bits 2t.
   const long long w = idx >> 4;
-  const uint32_t lo = __ldg(words + w), hi = __ldg(words + w + 1);
+  const uint32_t lo = ldg_word(words, w), hi = ldg_word(words, w + 1);
   return __funnelshift_r(lo, hi, (unsigned)(idx & 15) * 2u);
 }
 
 __device__ __forceinline__ int base_at(const uint32_t* __restrict__ words, long long idx) {
-  return (int)((__ldg(words + (idx >> 4)) >> ((unsigned)(idx & 15) * 2u)) & 3u);
+  return (int)((ldg_word(words, idx >> 4) >> ((unsigned)(idx & 15) * 2u)) & 3u);
 }
 
 constexpr int kMaxClockedWarps = 1 << 16;
@@ -257,7 +292,7 @@ __device__ bool extend_warp(const uint32_t* __restrict__ words, const Item& it, 
 // slots are processed top down so the slot below still holds d-1.  The lowest
 // chunk's lane 0 reads its new b base from memory.
 __device__ __forceinline__ int base_of(const uint32_t* __restrict__ words, long long idx) {
-  return (int)((__ldg(words + (idx >> 4)) >> ((unsigned)(idx & 15) * 2u)) & 3u);
+  return (int)((ldg_word(words, idx >> 4) >> ((unsigned)(idx & 15) * 2u)) & 3u);
 }
 
 template <int NC>
@@ -520,7 +555,7 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
       const int r = b_rel - d + 64 * c0;  // lane 0, low cell of slot 1: store index b_lo - d + 64*c0
       if ((r >> 4) != bq_idx) {  // r falls by one per antidiagonal: one load per 16
         bq_idx = r >> 4;
-        bq = __ldg(bwords + bq_idx);
+        bq = ldg_word(words, (long long)(bwords - words) + bq_idx);
       }
       const int bfresh = (int)((bq >> ((unsigned)(r & 15) * 2u)) & 3u);
       unsigned prev_top = 0;
@@ -706,6 +741,7 @@ struct NarrowLane {
 
 template <int WT, typename T>
 __device__ __forceinline__ T& nslot(T* wbase, int A, int s, int lane) {
+  if (!DIBELLA_IN_BOUNDS(s, WT, 1)) s = 0;
   return wbase[((A * WT + s) << 5) + lane];
 }
 
@@ -828,8 +864,12 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
     const unsigned q = pop_warp(p.cnt, p.wide_q_id);
     if (q >= tail) break;
     const int item = p.wide_q[q];
+    if (!DIBELLA_IN_BOUNDS(item, p.q_cap, 3)) continue;
     if (fwd) {
-      if (lane == 0) p.esc_q[atomicAdd(&p.cnt->tail[p.esc_q_id], 1u)] = item;
+      if (lane == 0) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = item;
+      }
       __syncwarp();
       continue;
     }
@@ -837,7 +877,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
     if (!extend_reg<NC>(p.words, it, p.sc, p.ext + item)) {
       if (lane == 0) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-        p.esc_q[s] = item;
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = item;
         atomicAdd(&p.cnt->stat[3], 1u);
       }
     } else if (lane == 0) {
@@ -864,8 +904,12 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
     const unsigned q = pop_warp(p.cnt, p.wide_q_id);
     if (q >= tail) break;
     const int item = p.wide_q[q];
+    if (!DIBELLA_IN_BOUNDS(item, p.q_cap, 3)) continue;
     if (fwd) {
-      if (lane == 0) p.esc_q[atomicAdd(&p.cnt->tail[p.esc_q_id], 1u)] = item;
+      if (lane == 0) {
+        const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = item;
+      }
       __syncwarp();
       continue;
     }
@@ -873,7 +917,7 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
     if (!extend_pk<NC>(p.words, it, p.sc, p.ext + item)) {
       if (lane == 0) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-        p.esc_q[s] = item;
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = item;
         atomicAdd(&p.cnt->stat[3], 1u);
       }
     } else if (lane == 0) {
@@ -963,6 +1007,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
       if (want) {
         if (q < tail) {
           item = p.wide_q[q];
+          if (!DIBELLA_IN_BOUNDS(item, p.q_cap, 3)) item = 0;
           const Item it = p.items[item];
           m = it.m;
           n = it.n;
@@ -1043,7 +1088,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
       if (rare && cneed - cbase > NC - 1) {  // band outgrew the slots: hand over
         if (gl == 0) {
           const unsigned s2 = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-          p.esc_q[s2] = item;
+          if (DIBELLA_IN_BOUNDS(s2, p.q_cap, 2)) p.esc_q[s2] = item;
           atomicAdd(&p.cnt->stat[3], 1u);
         }
         active = false;
@@ -1102,7 +1147,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
       const long long r = b_lo - d + CH * c0;  // lane 0 of the group, low cell of slot 1
       if ((r >> 4) != (long long)bq_idx) {
         bq_idx = (int)(r >> 4);
-        bq = active ? __ldg(words + (r >> 4)) : 0u;
+        bq = active ? ldg_word(words, r >> 4) : 0u;
       }
       const unsigned bfresh = (bq >> ((unsigned)(r & 15) * 2u)) & 3u;
       unsigned prev_top = 0;
@@ -1385,6 +1430,7 @@ __global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
     if (threadIdx.x == 0) {
       const unsigned q = atomicAdd(&p.cnt->head[p.wide_q_id], 1u);
       sh.item = q < tail ? p.wide_q[q] : -1;
+      if (sh.item >= 0 && !DIBELLA_IN_BOUNDS(sh.item, p.q_cap, 3)) sh.item = -1;
     }
     __syncthreads();
     const int item = sh.item;
@@ -1394,7 +1440,7 @@ __global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
     if (!extend_cta(p.words, it, p.sc, sh, arr, p.ext + item)) {
       if (threadIdx.x == 0) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-        p.esc_q[s] = item;
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = item;
         atomicAdd(&p.cnt->stat[4], 1u);
       }
     } else if (threadIdx.x == 0) {
@@ -1428,8 +1474,9 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
       base = __shfl_sync(kFull, base, leader);
       if (want & (1u << lane)) {
         const unsigned q = base + __popc(want & ((1u << lane) - 1u));
-        if (q < ntail) {
-          const int item = p.narrow_q[q];
+        const int item = q < ntail ? p.narrow_q[q] : -1;
+        // (a bad item index, debug build: dropped; the lane stays idle and refills)
+        if (q < ntail && DIBELLA_IN_BOUNDS(item, p.q_cap, 3)) {
           const Item it = p.items[item];
           narrow_init<WT, T>(L, it, item, wbase, lane);
           active = true;
@@ -1439,7 +1486,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
             p.ext[item] = o;
             active = false;
           }
-        } else {
+        } else if (q >= ntail) {
           exhausted = true;
         }
       }
@@ -1461,7 +1508,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
         active = false;
       } else if (r == 2) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
-        p.esc_q[s] = L.item;
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = L.item;
         atomicAdd(&p.cnt->stat[p.narrow_esc_stat], 1u);
         active = false;
       }
@@ -1472,12 +1519,14 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
 // Global-band form: one warp per extension, band in workspace memory.
 __global__ void __launch_bounds__(kBlockThreads) global_kernel(ExtendParams p) {
   const int gwarp = (blockIdx.x * kBlockThreads + threadIdx.x) >> 5;
+  if (!DIBELLA_IN_BOUNDS(gwarp, kGlobalWarps, 5)) return;
   int* arr = p.gband + (size_t)gwarp * 3 * p.gcap;
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   for (;;) {
     const unsigned q = pop_warp(p.cnt, p.wide_q_id);
     if (q >= tail) break;
     const int item = p.wide_q[q];
+    if (!DIBELLA_IN_BOUNDS(item, p.q_cap, 3)) continue;
     const Item it = p.items[item];
     if (!extend_warp<true>(p.words, it, p.sc, arr, p.gcap, p.ext + item)) {
       if ((threadIdx.x & 31) == 0) {
@@ -1513,7 +1562,7 @@ struct ExpandParams {
 __device__ __forceinline__ unsigned long long bases64(const uint32_t* __restrict__ words, long long idx) {
   const long long w = idx >> 4;
   const unsigned sh = (unsigned)(idx & 15) * 2u;
-  const uint32_t w0 = __ldg(words + w), w1 = __ldg(words + w + 1), w2 = __ldg(words + w + 2);
+  const uint32_t w0 = ldg_word(words, w), w1 = ldg_word(words, w + 1), w2 = ldg_word(words, w + 2);
   return (unsigned long long)__funnelshift_r(w0, w1, sh) |
          ((unsigned long long)__funnelshift_r(w1, w2, sh) << 32);
 }
@@ -1605,6 +1654,26 @@ __global__ void scatter_kernel(const Item* __restrict__ items, long long n_items
     const unsigned s = atomicAdd(&cnt->bucket_cursor[cls][b], 1u);
     (cls == 0 ? narrow_q : wide_q)[s] = (int)t;
   }
+}
+
+#ifdef DIBELLA_BOUNDS_CHECK
+// Debug build: the words of the batch's store (the last read's two copies end
+// it, followed by the 8 closing zero words), for the store-read checks.
+__global__ void store_extent_kernel(const long long* offs, const int* lens, long long n_reads) {
+  g_store_words = n_reads > 0 ? offs[n_reads - 1] + 2 * copy_words(lens[n_reads - 1]) + 8 : 8;
+}
+#endif
+
+// Debug build: set the store extent on `st` (no launch in the release build).
+void set_store_extent(const int64_t* offs, const int32_t* lens, int64_t n_reads, cudaStream_t st) {
+#ifdef DIBELLA_BOUNDS_CHECK
+  store_extent_kernel<<<1, 1, 0, st>>>((const long long*)offs, lens, (long long)n_reads);
+#else
+  (void)offs;
+  (void)lens;
+  (void)n_reads;
+  (void)st;
+#endif
 }
 
 struct CombineParams {
@@ -2298,6 +2367,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   }
   g_launches = 0;
   record(st, 0);
+  set_store_extent(read_word_offsets, read_lengths, n_reads, st);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
                         scoring, results, ws, L, sch, st);
   if (rc != DIBELLA_OK) return rc;
@@ -2315,6 +2385,7 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.forward_max = 0;
   ep.cells_idx = 1;
   ep.wclock = nullptr;
+  ep.q_cap = 2 * n_pairs;
   int* q[kNumQ];
   for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
@@ -2446,6 +2517,7 @@ int dibella_xdrop_per_pair(const uint32_t* packed_words, const int64_t* read_wor
   cudaStream_t st = (cudaStream_t)stream;
   dibella_schedule_t sch;
   dibella_get_default_schedule(&sch);
+  set_store_extent(read_word_offsets, read_lengths, n_reads, st);
   rc = expand_and_queue(packed_words, read_word_offsets, read_lengths, n_reads, pairs, n_pairs, k,
                         scoring, results, ws, L, sch, st);
   if (rc != DIBELLA_OK) return rc;
@@ -2632,6 +2704,26 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
 
 int dibella_last_launch_count(void) { return g_launches; }
 
+int dibella_bounds_check(int64_t* out, int reset) {
+  if (!out) return DIBELLA_EINVAL;
+  for (int i = 0; i < 4; ++i) out[i] = 0;
+#ifdef DIBELLA_BOUNDS_CHECK
+  unsigned long long v[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(v, g_bounds_fault, sizeof(v));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long z[4] = {0, 0, 0, 0};
+    e = cudaMemcpyToSymbol(g_bounds_fault, z, sizeof(z));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "bounds record");
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
+  return 1;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
+
 int dibella_enable_warp_clock(int launch) {
   if (launch < 0 || launch > 4) return DIBELLA_EINVAL;
   g_clock_launch = launch;
@@ -2651,6 +2743,12 @@ int dibella_warp_clock(uint64_t* out, int max_warps) {
 
 const char* dibella_last_error(void) { return g_last_error.c_str(); }
 
-const char* dibella_version(void) { return "dibella-gb300 0.1.0 (sm_103a)"; }
+const char* dibella_version(void) {
+#ifdef DIBELLA_BOUNDS_CHECK
+  return "dibella-gb300 0.2.0 (sm_103a, bounds-checked debug build)";
+#else
+  return "dibella-gb300 0.2.0 (sm_103a)";
+#endif
+}
 
 }  // extern "C"

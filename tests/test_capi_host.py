@@ -35,6 +35,18 @@ def test_library_exports_every_declared_symbol():
         assert callable(getattr(dib, name)), name
 
 
+def test_debug_library_exports_the_same_symbols():
+    """The bounds-checked build (libdibella_debug.so) is the same C ABI."""
+    import ctypes
+    from paper_2001_10049_gb300 import _build
+    path = _build.build(debug=True)
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    lib.dibella_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in lib.dibella_version()
+
+
 def test_version_and_error_string():
     assert "sm_103a" in dib.dibella_version()
     assert isinstance(dib.dibella_last_error(), str)
