@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--sample-pairs", type=int, default=0,
                     help="align a seeded sample of this many candidate pairs instead of all")
     ap.add_argument("--schedule", default=None, help="JSON dict overriding the default schedule")
-    ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve", "candidates"], default="batch",
+    ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve", "candidates", "traceback"],
+                    default="batch",
                     help="batch: the benchmark line (E. coli-sized, X=7 and 25); tune: uneven-length batch, "
                          "fixed vs autotuned schedule; stream: repeat-rich pairs streamed in chunks; "
                          "serve: continuous-batching request loop at three offered loads; candidates: GPU "
@@ -89,6 +90,7 @@ def parse():
                     help="stream mode: override the genome length (repeat content scaled with it)")
     ap.add_argument("--n-parts", type=int, default=8, help="stream mode: hash passes of the k-mer count")
     ap.add_argument("--tune-workload", default="c3_uneven", help="tune mode: workload")
+    ap.add_argument("--trace-seeds", type=int, default=20000, help="traceback mode: accepted seeds traced")
     ap.add_argument("--tune-x", type=int, default=50, help="tune mode: X-drop")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -367,6 +369,75 @@ def mode_tune(args):
         "speedup_tuned_vs_naive": naive_ms / tuned_ms,
         "speedup_fixed_vs_naive": naive_ms / fixed_ms,
         "clocks": clocks.summary(),
+    }))
+
+
+def mode_traceback(args):
+    """Traceback of accepted overlaps (the edits of each best alignment,
+    diBELLA Sec. 1-2): the best seed of every E. coli-sized candidate pair whose
+    X = 25 alignment spans at least 2 kb of A at a score of at least 0.4 per
+    column of A (true overlaps; pairs that share a k-mer by chance score near
+    0 per column), a seeded sample of them, aligned again with every cell's
+    move kept and walked back on the GPU (dibella_xdrop_traceback, a warp per
+    seed).  value = seeds traced per second; the cell rate and the bytes of
+    the move stream per cell go with it."""
+    import torch
+    import paper_2001_10049_gb300 as dib
+    dev = torch.device("cuda", 0)
+    X = 25
+    w = workloads.generate(WORKLOAD)
+    store = dib.ReadStore.from_ascii(w.reads, w.offsets, device=dev)
+    al = dib.Aligner(store, len(w.pairs), k=K, device=dev)
+    res = al.align(w.pairs, dib.Scoring(1, -1, -1, X))
+    span = res["end_a"].astype(np.int64) - res["begin_a"].astype(np.int64)
+    acc = np.flatnonzero(((res["status"] & 4) != 0) & (span >= 2000) & (res["score"] >= 0.4 * span))
+    rng = np.random.default_rng(31)
+    pick = np.sort(rng.choice(acc, size=min(args.trace_seeds, len(acc)), replace=False))
+    seeds = w.pairs[pick]
+    n = len(seeds)
+    lanes = min(n, 8 * torch.cuda.get_device_properties(dev).multi_processor_count)
+    moves_words = 1 << 20
+    tal = dib.Aligner(store, n, k=K, device=dev)
+    tal.upload_pairs(seeds)
+    ops_per_seed = 4096
+    ops = torch.zeros((n, ops_per_seed), dtype=torch.int32, device=dev)
+    n_ops = torch.zeros(n, dtype=torch.int32, device=dev)
+    ws_bytes = dib.dibella_traceback_workspace_bytes(lanes, store.max_len, moves_words)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    sc = dib.Scoring(1, -1, -1, X)
+    stream = torch.cuda.Stream(device=dev)
+    times = []
+    with ClockSampler(0) as clocks:
+        for r in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dib.dibella_xdrop_traceback(store.words, store.word_offsets, store.lengths, store.n_reads,
+                                            store.max_len, tal.pairs, n, K, sc, tal.results, ops, ops_per_seed,
+                                            n_ops, lanes, moves_words, ws, ws_bytes, stream=stream)
+                e1.record(stream)
+            e1.synchronize()
+            if r >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    tres = tal.results_host(n)
+    nops = n_ops.cpu().numpy()
+    same = bool(((tres["score"] == res["score"][pick]) & (tres["end_a"] == res["end_a"][pick])).all())
+    cells = int(tres["cells"].sum())
+    # moves up to each best cell: 3 words per antidiagonal + 2 bits per cell (upper bound: every antidiagonal)
+    antidiag = int((tres["end_a"].astype(np.int64) - tres["begin_a"] + tres["end_b"] - tres["begin_b"]).sum())
+    stream_bytes = 4 * 3 * antidiag + cells / 4
+    print(json.dumps({
+        "metric": "traced seeds/s", "mode": "traceback", "value": n / (ms * 1e-3), "unit": "seeds/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "gcups": cells / (ms * 1e-3) / 1e9, "ms": ms,
+        "config": {"workload": WORKLOAD + " accepted overlaps (best seed, >= 2 kb of A, score >= 0.4 per column)",
+                   "accepted": int(len(acc)), "seeds": n, "xdrop": X, "warps": lanes,
+                   "moves_words_per_warp": moves_words, "ops_per_seed": ops_per_seed, "steps": args.steps},
+        "cells": cells, "runs": int(nops[nops > 0].sum()), "seeds_complete": int((nops > 0).sum()),
+        "move_stream_bytes_per_cell": stream_bytes / max(cells, 1),
+        "move_stream_gbs": stream_bytes / (ms * 1e-3) / 1e9,
+        "results_equal_batch": same, "clocks": clocks.summary(),
     }))
 
 
@@ -688,7 +759,7 @@ def main():
         return
     if args.mode != "batch":
         if rank == 0:
-            {"tune": mode_tune,
+            {"tune": mode_tune, "traceback": mode_traceback,
              "stream": mode_stream if args.stream_workload == "c4_repeats_small" else mode_stream_full,
              "serve": mode_serve,
              "candidates": mode_candidates}[args.mode](args)

@@ -410,10 +410,15 @@ int dibella_traceback_workspace_bytes(int64_t n_lanes, int32_t max_read_len, int
  * extension's moves up to its best cell exceeded moves_words; -3 when a read
  * is longer than max_read_len, the result then carries
  * DIBELLA_RES_BAND_OVERFLOW and zero fields).  Asynchronous on `stream`
- * (a cudaStream_t); allocates nothing.  A thread per seed (n_lanes threads,
- * each with one workspace slot) re-runs both extensions serially: a first
- * form, meant for the seeds whose edits are wanted (accepted overlaps), not
- * for whole candidate batches.  EINVAL on the scoring limits of
+ * (a cudaStream_t); allocates nothing.  A warp per seed (n_lanes warps,
+ * each with one workspace slot, taking seeds t = w, w + n_lanes, ...)
+ * re-runs both extensions with the band across its lanes, then one lane walks
+ * back: meant for the seeds whose edits are wanted (accepted overlaps).
+ * Sizing: n_lanes of 4 to 8 warps per SM keeps the GPU busy (e.g. 1,024 on
+ * 152 SMs); moves_words must hold, per extension, 3 words per antidiagonal up
+ * to the best one plus 2 bits per evaluated cell, about (m + n) x (3 + band /
+ * 16) words for an m x n extension (2^18 words cover a 30 kb overlap at a
+ * 40-cell band).  EINVAL on the scoring limits of
  * dibella_xdrop_batch, k outside 1..32, ops_per_seed < 1, null or
  * misaligned (256-byte) pointers or a size outside the limits above; ENOMEM
  * when workspace_bytes is below dibella_traceback_workspace_bytes. */
@@ -466,8 +471,10 @@ int dibella_phase_times(float* ms_out, int n_max);
  * forms, out[10] and out[11] the part of out[7] finished by the wide launch
  * on the escalations and by the slot-ladder rungs, out[12] the cells of the
  * extensions finished by the mid form, out[13] extensions that outgrew the
- * mid form.  Returns the number written (<= n_max, at most 14), or a
- * negative status. */
+ * mid form, out[14] the cells the narrow and mid forms evaluated for the
+ * extensions they handed on (restarted from the origin by the wider form, so
+ * evaluated twice; not part of the cells of any result).  Returns the number
+ * written (<= n_max, at most 15), or a negative status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 
 /* Number of kernels the calling thread's last dibella_xdrop_batch (or _host /

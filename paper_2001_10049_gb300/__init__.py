@@ -392,13 +392,13 @@ def dibella_phase_times(n_max: int = 8) -> list[float]:
 
 
 def dibella_batch_counters(workspace, stream=None) -> dict:
-    buf = (ctypes.c_int64 * 14)()
-    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 14)
+    buf = (ctypes.c_int64 * 15)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 15)
     if n < 0:
         _check(n, "dibella_batch_counters")
     keys = ["narrow", "wide", "escalated_narrow", "escalated_wide", "escalated_smem", "band_overflow",
             "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder",
-            "cells_mid", "escalated_mid"]
+            "cells_mid", "escalated_mid", "cells_restarted"]
     return {keys[i]: int(buf[i]) for i in range(n)}
 
 

@@ -10,14 +10,13 @@
 // the diagonal first, then the step in A, then the step in B' on equal
 // values.  The walk from the best cell back to the seed follows those moves.
 //
-// First form: one thread per seed re-runs both extensions serially.  Its
-// scratch (a slot of the caller's workspace per thread) holds three rows of
-// H indexed by the position in A, and a stream of 32-bit words with, per
-// evaluated antidiagonal, two header words (the band's first i and its
-// width), the band's moves at 2 bits per cell, and a trailer word (the width
-// again), so that the walk can step back one antidiagonal at a time.  The
-// per-seed code is __host__ __device__; the library launches it only on the
-// GPU.
+// A warp per seed re-runs both extensions with the band's cells across its
+// lanes.  Its scratch (a slot of the caller's workspace per warp) holds three
+// rows of H indexed by the position in A, read and written coalesced, and a
+// stream of 32-bit words with, per evaluated antidiagonal, two header words
+// (the band's first i and its width), the band's moves at 2 bits per cell
+// (packed by warp reductions), and a trailer word (the width again), so that
+// lane 0 can walk back one antidiagonal at a time from the best cell.
 
 #include <cuda_runtime.h>
 
@@ -74,18 +73,26 @@ struct TbExt {
   bool recorded;       // every antidiagonal up to the best one fit the stream
 };
 
-// The X-drop extension from the origin, recording moves into mv (capacity
-// cap words) while they fit.
-__host__ __device__ TbExt tb_extend(const TbArgs& p, const TbSeq& s, int32_t* r0, int32_t* r1, int32_t* r2,
-                                    uint32_t* mv, long long cap) {
+// The X-drop extension from the origin, run by the 32 lanes of a warp (every
+// lane calls it; lane l computes cell i = i0 + l of each 32-cell chunk of the
+// band), recording moves into mv (capacity cap words) while they fit.  The
+// rows r0..r2 (antidiagonals d, d-1, d-2, indexed by i) live in the warp's
+// workspace slot, read and written coalesced.  Each chunk's 2-bit moves are
+// packed 16 cells to a word by two warp OR-reductions; lane 0 writes the
+// stream, so its format is the one tb_walk reads.  All lanes return the same
+// result.
+__device__ TbExt tb_extend_warp(const TbArgs& p, const TbSeq& s, int32_t* r0, int32_t* r1, int32_t* r2,
+                                uint32_t* mv, long long cap) {
+  constexpr unsigned kAll = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
   TbExt e{0, 0, 0, 0, -1, true};
-  // rows: r2 = antidiagonal d-2, r1 = d-1, r0 = d; band [lo, hi] of each
   int lo2 = 1, hi2 = 0, lo1 = 0, hi1 = 0;
-  r1[0] = 0;
+  if (lane == 0) r1[0] = 0;
+  __syncwarp();
   int live_lo = 0, live_hi = 0;
   int best = 0;
-  long long w = 0;        // stream words written
-  bool streaming = true;  // every antidiagonal so far fit the stream
+  long long w = 0;
+  bool streaming = true;
   const int last_d = s.m + s.n;
   for (int d = 1; d <= last_d; ++d) {
     int lo = live_lo > d - s.n ? live_lo : d - s.n;
@@ -97,54 +104,66 @@ __host__ __device__ TbExt tb_extend(const TbArgs& p, const TbSeq& s, int32_t* r0
     const long long rec = w;
     const bool keep = streaming && w + 3 + (width + 15) / 16 <= cap;
     streaming = keep;
-    if (keep) {
-      mv[w++] = (uint32_t)lo;
-      mv[w++] = (uint32_t)width;
+    if (keep && lane == 0) {
+      mv[w] = (uint32_t)lo;
+      mv[w + 1] = (uint32_t)width;
     }
+    if (keep) w += 2;
     const int threshold = best - p.X;
     int row_best = kDead, row_best_i = -1, new_lo = -1, new_hi = -1;
-    uint32_t pack = 0;
-    for (int i = lo; i <= hi; ++i) {
+    for (int i0 = lo; i0 <= hi; i0 += 32) {
+      const int i = i0 + lane;
       const int j = d - i;
       int h = kDead;
       uint32_t from = kMoveNone;
-      if (i >= 1 && j >= 1 && i - 1 >= lo2 && i - 1 <= hi2 && r2[i - 1] != kDead) {
-        const uint32_t x = tb_base(p.words, s.a0, (long long)s.sa * (i - 1));
-        const uint32_t y = tb_base(p.words, s.b0, (long long)s.sb * (j - 1));
-        const int v = r2[i - 1] + (x == y ? p.M : p.S);
-        if (v > h) {
-          h = v;
-          from = kMoveDiag;
+      bool live = false;
+      if (i <= hi) {
+        if (i >= 1 && j >= 1 && i - 1 >= lo2 && i - 1 <= hi2 && r2[i - 1] != kDead) {
+          const uint32_t x = tb_base(p.words, s.a0, (long long)s.sa * (i - 1));
+          const uint32_t y = tb_base(p.words, s.b0, (long long)s.sb * (j - 1));
+          const int v = r2[i - 1] + (x == y ? p.M : p.S);
+          if (v > h) {
+            h = v;
+            from = kMoveDiag;
+          }
+        }
+        if (i >= 1 && i - 1 >= lo1 && i - 1 <= hi1 && r1[i - 1] != kDead && r1[i - 1] + p.G > h) {
+          h = r1[i - 1] + p.G;
+          from = kMoveA;
+        }
+        if (j >= 1 && i >= lo1 && i <= hi1 && r1[i] != kDead && r1[i] + p.G > h) {
+          h = r1[i] + p.G;
+          from = kMoveB;
+        }
+        live = h != kDead && h >= threshold;
+        r0[i] = live ? h : kDead;
+      }
+      const uint32_t bits = live ? from : kMoveNone;
+      const uint32_t wlo = __reduce_or_sync(kAll, lane < 16 ? bits << (2 * lane) : 0u);
+      const uint32_t whi = __reduce_or_sync(kAll, lane >= 16 ? bits << (2 * (lane - 16)) : 0u);
+      const int c0 = i0 - lo;  // cell offset of the chunk; a multiple of 32
+      if (keep && lane == 0) {
+        mv[w + c0 / 16] = wlo;
+        if (c0 + 16 < width) mv[w + c0 / 16 + 1] = whi;
+      }
+      const unsigned bl = __ballot_sync(kAll, live);
+      if (bl) {
+        if (new_lo < 0) new_lo = i0 + __ffs(bl) - 1;
+        new_hi = i0 + 31 - __clz(bl);
+        const int cmax = __reduce_max_sync(kAll, live ? h : kDead);
+        if (cmax > row_best) {  // strictly larger: an earlier chunk (smaller i) keeps a tie
+          row_best = cmax;
+          row_best_i = i0 + __ffs(__ballot_sync(kAll, live && h == cmax)) - 1;
         }
       }
-      if (i >= 1 && i - 1 >= lo1 && i - 1 <= hi1 && r1[i - 1] != kDead && r1[i - 1] + p.G > h) {
-        h = r1[i - 1] + p.G;
-        from = kMoveA;
-      }
-      if (j >= 1 && i >= lo1 && i <= hi1 && r1[i] != kDead && r1[i] + p.G > h) {
-        h = r1[i] + p.G;
-        from = kMoveB;
-      }
-      e.cells += 1;
-      const bool live = h != kDead && h >= threshold;
-      r0[i] = live ? h : kDead;
-      const int c = i - lo;
-      pack |= (live ? from : kMoveNone) << (2 * (c & 15));
-      if (((c & 15) == 15 || i == hi) && keep) {
-        mv[w++] = pack;
-        pack = 0;
-      } else if ((c & 15) == 15 || i == hi) {
-        pack = 0;
-      }
-      if (!live) continue;
-      if (new_lo < 0) new_lo = i;
-      new_hi = i;
-      if (h > row_best) {
-        row_best = h;
-        row_best_i = i;
-      }
     }
-    if (keep) mv[w++] = (uint32_t)width;
+    e.cells += width;
+    if (keep) {
+      w += (width + 15) / 16;
+      if (lane == 0) mv[w] = (uint32_t)width;
+      w += 1;
+    }
+    __syncwarp();  // the row of d is complete before any lane reads it as d-1
     if (new_lo < 0) break;
     if (row_best > best) {
       best = row_best;
@@ -238,10 +257,12 @@ __host__ __device__ bool tb_walk(const TbArgs& p, const TbSeq& s, const TbExt& e
   return true;
 }
 
-// Everything for seed t with one lane's scratch: the result record (as
-// dibella_xdrop_batch writes it, without the best-of-pair flag) and the
-// run-length encoded columns from (begin_a, begin_b') to (end_a, end_b').
-__host__ __device__ void tb_seed(const TbArgs& p, long long t, char* scratch) {
+// Everything for seed t with one warp and its workspace slot: the result
+// record (as dibella_xdrop_batch writes it, without the best-of-pair flag) and
+// the run-length encoded columns from (begin_a, begin_b') to (end_a, end_b').
+// Every lane runs both extensions; lane 0 walks back and writes.
+__device__ void tb_seed(const TbArgs& p, long long t, char* scratch) {
+  const int lane = threadIdx.x & 31;
   const dibella_pair_t pr = p.pairs[t];
   dibella_result_t r;
   r.score = r.score_left = r.score_right = 0;
@@ -258,14 +279,18 @@ __host__ __device__ void tb_seed(const TbArgs& p, long long t, char* scratch) {
   }
   if (!valid) {
     r.status = DIBELLA_RES_INVALID_SEED;
-    p.results[t] = r;
-    p.n_ops[t] = 0;
+    if (lane == 0) {
+      p.results[t] = r;
+      p.n_ops[t] = 0;
+    }
     return;
   }
   if (lenA > p.max_len || lenB > p.max_len) {  // the H rows would not hold the band
     r.status = DIBELLA_RES_BAND_OVERFLOW;
-    p.results[t] = r;
-    p.n_ops[t] = -3;
+    if (lane == 0) {
+      p.results[t] = r;
+      p.n_ops[t] = -3;
+    }
     return;
   }
   const long long fA = p.word_offsets[pr.read_a] * 16;
@@ -290,22 +315,27 @@ __host__ __device__ void tb_seed(const TbArgs& p, long long t, char* scratch) {
   bool ok = true;
   // The left walk runs from its best cell (the alignment's start) toward the
   // seed: its columns come out in alignment order.
-  const TbExt el = tb_extend(p, L, rows, rows + hw, rows + 2 * hw, mv, p.moves_words);
-  ok = el.recorded && tb_walk(p, L, el, mv, &runs);
-  for (int q = 0; q < k && ok; ++q)
-    runs.push(tb_base(p.words, fA, pa + q) == tb_base(p.words, bp0, pb + q) ? kOpEq : kOpX);
+  const TbExt el = tb_extend_warp(p, L, rows, rows + hw, rows + 2 * hw, mv, p.moves_words);
+  if (lane == 0) {
+    ok = el.recorded && tb_walk(p, L, el, mv, &runs);
+    for (int q = 0; q < k && ok; ++q)
+      runs.push(tb_base(p.words, fA, pa + q) == tb_base(p.words, bp0, pb + q) ? kOpEq : kOpX);
+  }
+  __syncwarp();  // the left walk has read the stream before the right extension rewrites it
   // The right walk yields its columns last to first: its runs go to the H
   // rows (free once the extension is done; at most m + n runs fit there),
   // then into the seed's runs in reverse order.
-  const TbExt er = tb_extend(p, R, rows, rows + hw, rows + 2 * hw, mv, p.moves_words);
-  if (ok) {
-    TbRuns back{(uint32_t*)rows, (int)(3 * hw < 0x7FFFFFFF ? 3 * hw : 0x7FFFFFFF), 0, false, 0, 0};
-    ok = er.recorded && tb_walk(p, R, er, mv, &back);
-    back.flush();
-    ok = ok && !back.full;
-    for (int x = back.n - 1; x >= 0 && ok; --x) runs.push_run(back.out[x] & 15u, back.out[x] >> 4);
+  const TbExt er = tb_extend_warp(p, R, rows, rows + hw, rows + 2 * hw, mv, p.moves_words);
+  if (lane == 0) {
+    if (ok) {
+      TbRuns back{(uint32_t*)rows, (int)(3 * hw < 0x7FFFFFFF ? 3 * hw : 0x7FFFFFFF), 0, false, 0, 0};
+      ok = er.recorded && tb_walk(p, R, er, mv, &back);
+      back.flush();
+      ok = ok && !back.full;
+      for (int x = back.n - 1; x >= 0 && ok; --x) runs.push_run(back.out[x] & 15u, back.out[x] >> 4);
+    }
+    runs.flush();
   }
-  runs.flush();
   r.score = seed + el.best + er.best;
   r.score_left = el.best;
   r.score_right = er.best;
@@ -316,15 +346,20 @@ __host__ __device__ void tb_seed(const TbArgs& p, long long t, char* scratch) {
   r.end_b = (uint32_t)(pr.strand ? lenB - bb : eb);
   r.status = exact ? 0 : DIBELLA_RES_SEED_MISMATCH;
   r.cells = el.cells + er.cells;
-  p.results[t] = r;
-  p.n_ops[t] = !ok ? -2 : (runs.full ? -1 : runs.n);
+  if (lane == 0) {
+    p.results[t] = r;
+    p.n_ops[t] = !ok ? -2 : (runs.full ? -1 : runs.n);
+  }
+  __syncwarp();  // lane 0's use of the rows ends before the next seed
 }
 
+// A warp per seed: warp w (of n_lanes warps, one workspace slot each) takes
+// seeds w, w + n_lanes, ...
 __global__ void __launch_bounds__(kTbThreads) traceback_kernel(TbArgs p) {
-  const long long lane = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lane >= p.n_lanes) return;
-  char* scratch = p.workspace + lane * p.lane_bytes;
-  for (long long t = lane; t < p.n_pairs; t += p.n_lanes) tb_seed(p, t, scratch);
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (warp >= p.n_lanes) return;
+  char* scratch = p.workspace + warp * p.lane_bytes;
+  for (long long t = warp; t < p.n_pairs; t += p.n_lanes) tb_seed(p, t, scratch);
 }
 
 long long tb_lane_bytes(long long max_len, long long moves_words) {
@@ -387,7 +422,7 @@ int dibella_xdrop_traceback(const uint32_t* packed_words, const int64_t* read_wo
   a.moves_words = moves_words;
   a.workspace = (char*)workspace;
   a.lane_bytes = tb_lane_bytes(max_read_len, moves_words);
-  const long long blocks = (a.n_lanes + kTbThreads - 1) / kTbThreads;
+  const long long blocks = (a.n_lanes * 32 + kTbThreads - 1) / kTbThreads;
   traceback_kernel<<<(unsigned)blocks, kTbThreads, 0, (cudaStream_t)stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? DIBELLA_OK : DIBELLA_ECUDA;
 }

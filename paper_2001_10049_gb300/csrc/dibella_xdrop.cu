@@ -84,7 +84,9 @@ struct Counters {
                           // shared-memory form, band overflows, escalated from the mid form
   // cells of finished extensions: 0 narrow, 1 wide (first launch), 2 CTA,
   // 3 global, 4 wide launch on the narrow escalations, 5 slot-ladder rungs,
-  // 6 mid form (the narrow escalations, one lane per extension, wide band)
+  // 6 mid form (the narrow escalations, one lane per extension, wide band),
+  // 7 cells the one-lane forms evaluated for extensions they then handed to a
+  // wider form (which restarts them: work done twice)
   unsigned long long cells[8];
 };
 
@@ -1510,6 +1512,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
         const unsigned s = atomicAdd(&p.cnt->tail[p.esc_q_id], 1u);
         if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.esc_q[s] = L.item;
         atomicAdd(&p.cnt->stat[p.narrow_esc_stat], 1u);
+        atomicAdd(&p.cnt->cells[7], (unsigned long long)L.cells);
         active = false;
       }
     }
@@ -2693,11 +2696,11 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
   e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const int64_t v[14] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
+  const int64_t v[15] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
                          (int64_t)c.cells[0], (int64_t)(c.cells[1] + c.cells[4] + c.cells[5]),
                          (int64_t)c.cells[2], (int64_t)c.cells[3], (int64_t)c.cells[4],
-                         (int64_t)c.cells[5], (int64_t)c.cells[6], c.stat[6]};
-  int n = std::min(n_max, 14);
+                         (int64_t)c.cells[5], (int64_t)c.cells[6], c.stat[6], (int64_t)c.cells[7]};
+  int n = std::min(n_max, 15);
   for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
 }
