@@ -75,7 +75,11 @@ def parse():
     ap.add_argument("--xdrops", default=",".join(str(x) for x in XDROPS))
     ap.add_argument("--sample-pairs", type=int, default=0,
                     help="align a seeded sample of this many candidate pairs instead of all")
-    ap.add_argument("--schedule", default=None, help="JSON dict overriding the default schedule")
+    ap.add_argument("--schedule", default=None, help="JSON dict: an explicit schedule (default schedule's fields "
+                                                     "overridden), passed to every call as given")
+    ap.add_argument("--default-schedule", default=None,
+                    help="JSON dict: fields set in the library's default schedule (the call still passes none, so "
+                         "the batch-size routing of the default applies)")
     ap.add_argument("--mode", choices=["batch", "tune", "stream", "serve", "candidates", "traceback"],
                     default="batch",
                     help="batch: the benchmark line (E. coli-sized, X=7 and 25); tune: uneven-length batch, "
@@ -783,6 +787,10 @@ def main():
         shard_info = {"cost_keys": [int(t) for t in totals], "max_over_mean": float(totals.max() / totals.mean())}
     n_seeds = len(pairs)
     sched = None
+    if args.default_schedule:
+        d = dib.dibella_get_default_schedule().as_dict()
+        d.update(json.loads(args.default_schedule))
+        dib.dibella_set_default_schedule(dib.Schedule.from_dict(d))
     if args.schedule:
         d = dib.dibella_get_default_schedule().as_dict()
         d.update(json.loads(args.schedule))
@@ -937,9 +945,12 @@ def main():
     # Roofline of the dominant kernel: integer ops of the cells its launch
     # finished / that launch's duration, from the phase events recorded on the
     # launching stream inside every replayed graph of the timed region.
-    # phases: 0 queueing, 1 narrow form, 2 first wide launch, 3 mid form, 4 wide
-    # launch on the escalations, 5 slot ladder + CTA + global forms, 6 combine
-    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 7]), axis=0) for X in XD}
+    # phases: 0 queueing, 1 narrow form, 2 its second pass, 3 first wide launch,
+    # 4 mid form, 5 wide launch on the escalations, 6 slot ladder + CTA + global
+    # forms, 7 combine; the narrow form's two passes are reported together
+    phase = {X: np.mean(np.array([ph for (x, _, ph) in log if x == X and len(ph) == 8]), axis=0) for X in XD}
+    for X in XD:
+        phase[X] = np.concatenate([phase[X][:1], [phase[X][1] + phase[X][2]], phase[X][3:]])
     batch_ms = {X: float(np.mean([ms for (x, ms, _) in log if x == X])) for X in XD}
     launch_cells = {X: {"narrow form": (1, counters[X]["cells_narrow"]),
                         "wide form, first launch": (2, counters[X]["cells_wide"] - counters[X]["cells_wide_esc"]

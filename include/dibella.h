@@ -126,6 +126,10 @@ int dibella_pack_reads(const char* ascii, const int64_t* ascii_offsets, int64_t 
  *           packed as int16 pairs when wide_packed is set and
  *           xdrop <= 8000 (exact: scores are kept relative to a moving base),
  *           else 32 int32 cells of one warp;
+ *   split   with narrow_split_d > 0 the narrow form runs in two passes: the
+ *           first stops every extension at antidiagonal narrow_split_d,
+ *           the second re-runs the unfinished ones from the origin, so that
+ *           long extensions share warps with long ones only;
  *   mid     the narrow form's escalations first go, when mid_band_cap > 0
  *           and xdrop <= 8000, to a second one-thread-per-extension form
  *           whose per-thread band holds mid_band_cap int16 cells (one warp
@@ -163,6 +167,8 @@ typedef struct {
   int32_t n_buckets;              /* 1..DIBELLA_MAX_BUCKETS                  */
   int32_t bucket_bounds[DIBELLA_MAX_BUCKETS];
   int32_t mid_band_cap;           /* mid form: 0 (none), 128, 192 or 256      */
+  int32_t narrow_split_d;         /* > 0: narrow form in two passes, the      */
+                                  /* first stopping at this antidiagonal      */
 } dibella_schedule_t;
 
 /* The schedule used when a call passes NULL.  set() validates (EINVAL). */
@@ -220,8 +226,8 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
  * that may not hold allocations of its own.  This entry point runs the same
  * alignment as dibella_xdrop_batch (same arguments, results and semantics,
  * default schedule) without any workspace from the caller and without
- * allocating.  Its scratch is one fixed array inside the library, 9,437,696
- * bytes (about 9.0 MiB), which every GPU that loads the library keeps until
+ * allocating.  Its scratch is one fixed array inside the library, 9,568,768
+ * bytes (about 9.1 MiB), which every GPU that loads the library keeps until
  * the process exits.
  * Limits: at most DIBELLA_NOALLOC_MAX_PAIRS seed records per call (more
  * returns DIBELLA_ENOMEM, with the reason in dibella_last_error(), and does
@@ -452,14 +458,15 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
 
 /* ---- diagnostics ------------------------------------------------------ */
 /* Phase timing: when enabled, dibella_xdrop_batch records CUDA events on
- * `stream` at eight points around its phases.  Under
+ * `stream` at nine points around its phases.  Under
  * stream capture they are recorded as external events, so a replayed CUDA
  * graph records them too.  dibella_phase_times() synchronises on the last
  * event and writes up to n_max phase durations in ms: queueing (expand, scan,
- * scatter), narrow form, first wide launch, mid form (0 without one), the
- * wide launch on the escalations, the slot ladder with the CTA and global
- * forms, combine; returns the count written (7 after a batch).  Enable it
- * before any capture (it creates the events). */
+ * scatter), narrow form (first pass), second narrow pass (0 without one),
+ * first wide launch, mid form (0 without one), the wide launch on the
+ * escalations, the slot ladder with the CTA and global forms, combine;
+ * returns the count written (8 after a batch).  Enable it before any capture
+ * (it creates the events). */
 int dibella_enable_phase_timing(int enable);
 int dibella_phase_times(float* ms_out, int n_max);
 
@@ -472,9 +479,11 @@ int dibella_phase_times(float* ms_out, int n_max);
  * on the escalations and by the slot-ladder rungs, out[12] the cells of the
  * extensions finished by the mid form, out[13] extensions that outgrew the
  * mid form, out[14] the cells the narrow and mid forms evaluated for the
- * extensions they handed on (restarted from the origin by the wider form, so
- * evaluated twice; not part of the cells of any result).  Returns the number
- * written (<= n_max, at most 15), or a negative status. */
+ * extensions they handed on (restarted from the origin by the wider form or
+ * the second narrow pass, so evaluated twice; not part of the cells of any
+ * result), out[15] the extensions the first narrow pass handed to the
+ * second.  Returns the number written (<= n_max, at most 16), or a negative
+ * status. */
 int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, int n_max);
 
 /* Number of kernels the calling thread's last dibella_xdrop_batch (or _host /
@@ -489,7 +498,7 @@ int dibella_last_launch_count(void);
  * 1 narrow form, 2 first wide launch, 3 mid form, 4 wide launch on the
  * escalations (0 = off), every later batch has each warp of that launch write
  * the GPU's global timer (ns) when it starts and when it finds its queue
- * empty and leaves.  dibella_warp_clock synchronises the device and copies
+ * empty and leaves (launch 5: the second narrow pass).  dibella_warp_clock synchronises the device and copies
  * the last clocked launch's (start, end) pairs, 2 x uint64 per warp, for at
  * most max_warps warps (65536 at most are clocked); returns the number of
  * warps written, or a negative status.  One clock array serves the process:

@@ -58,7 +58,8 @@ class Schedule(ctypes.Structure):
                 ("wide_packed", ctypes.c_int32), ("wide_group_lanes", ctypes.c_int32),
                 ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
-                ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS), ("mid_band_cap", ctypes.c_int32)]
+                ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS), ("mid_band_cap", ctypes.c_int32),
+                ("narrow_split_d", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
@@ -67,7 +68,7 @@ class Schedule(ctypes.Structure):
                 "wide_blocks_per_sm": self.wide_blocks_per_sm,
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
                 "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)],
-                "mid_band_cap": self.mid_band_cap}
+                "mid_band_cap": self.mid_band_cap, "narrow_split_d": self.narrow_split_d}
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
@@ -77,6 +78,7 @@ class Schedule(ctypes.Structure):
                     "narrow_blocks_per_sm", "n_buckets"):
             setattr(s, key, int(d[key]))
         s.mid_band_cap = int(d.get("mid_band_cap", 0))
+        s.narrow_split_d = int(d.get("narrow_split_d", 0))
         bounds = list(d.get("bucket_bounds", []))
         for b in range(MAX_BUCKETS):
             s.bucket_bounds[b] = int(bounds[b]) if b < len(bounds) else 0
@@ -392,18 +394,18 @@ def dibella_phase_times(n_max: int = 8) -> list[float]:
 
 
 def dibella_batch_counters(workspace, stream=None) -> dict:
-    buf = (ctypes.c_int64 * 15)()
-    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 15)
+    buf = (ctypes.c_int64 * 16)()
+    n = _lib().dibella_batch_counters(_ptr(workspace), _stream_handle(stream), buf, 16)
     if n < 0:
         _check(n, "dibella_batch_counters")
     keys = ["narrow", "wide", "escalated_narrow", "escalated_wide", "escalated_smem", "band_overflow",
             "cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_wide_esc", "cells_ladder",
-            "cells_mid", "escalated_mid", "cells_restarted"]
+            "cells_mid", "escalated_mid", "cells_restarted", "narrow_second_pass"]
     return {keys[i]: int(buf[i]) for i in range(n)}
 
 
-WARP_CLOCK_LAUNCHES = {"narrow form": 1, "wide form, first launch": 2, "mid form on the narrow escalations": 3,
-                       "wide form on the escalations": 4}
+WARP_CLOCK_LAUNCHES = {"narrow form": 1, "narrow form, second pass": 5, "wide form, first launch": 2,
+                       "mid form on the narrow escalations": 3, "wide form on the escalations": 4}
 
 
 def dibella_enable_warp_clock(launch: int) -> None:

@@ -71,8 +71,11 @@ static_assert(sizeof(ExtOut) == 24, "ext out is 24 bytes");
 // Queues: routed narrow / wide; narrow escalations (to the wide form); one
 // queue per step of the wide-form slot ladder (8 -> 16 -> 24 -> 32 slots);
 // the shared-memory form's input; the global-band form's input.
-// The mid form's escalations (extensions whose band outgrew it) go to kQEsc2.
-enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQLadder = 3, kQSmem = 7, kQGlobal = 8, kQEsc2 = 9, kNumQ = 10 };
+// The mid form's escalations (extensions whose band outgrew it) go to kQEsc2;
+// with a split narrow launch, the extensions still running after the first
+// pass's antidiagonal limit go to kQLong for the second pass.
+enum { kQNarrow = 0, kQWide = 1, kQEsc1 = 2, kQLadder = 3, kQSmem = 7, kQGlobal = 8, kQEsc2 = 9, kQLong = 10,
+       kNumQ = 11 };
 
 struct Counters {
   unsigned int tail[kNumQ];   // queue sizes (see the kQ* names)
@@ -81,7 +84,8 @@ struct Counters {
   unsigned int bucket_count[2][DIBELLA_MAX_BUCKETS];
   unsigned int bucket_cursor[2][DIBELLA_MAX_BUCKETS];
   unsigned int stat[8];   // routed narrow, routed wide, escalated from narrow / wide /
-                          // shared-memory form, band overflows, escalated from the mid form
+                          // shared-memory form, band overflows, escalated from the mid form,
+                          // moved to the second narrow pass
   // cells of finished extensions: 0 narrow, 1 wide (first launch), 2 CTA,
   // 3 global, 4 wide launch on the narrow escalations, 5 slot-ladder rungs,
   // 6 mid form (the narrow escalations, one lane per extension, wide band),
@@ -118,6 +122,11 @@ struct ExtendParams {
   // global timer (ns) when it starts, at [2w], and when it leaves, at [2w+1].
   unsigned long long* wclock;
   long long q_cap;  // entries of every queue and of items / ext (2 x seed records)
+  // Split narrow launch: an extension still running after antidiagonal
+  // narrow_max_d (0 = no limit) stops and goes to long_q, to be run again
+  // from the origin by the second pass.
+  int narrow_max_d;
+  int* long_q;
   Scoring sc;
   int* gband;
   int gcap;
@@ -1514,6 +1523,12 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
         atomicAdd(&p.cnt->stat[p.narrow_esc_stat], 1u);
         atomicAdd(&p.cnt->cells[7], (unsigned long long)L.cells);
         active = false;
+      } else if (p.narrow_max_d > 0 && L.d > p.narrow_max_d) {
+        const unsigned s = atomicAdd(&p.cnt->tail[kQLong], 1u);
+        if (DIBELLA_IN_BOUNDS(s, p.q_cap, 2)) p.long_q[s] = L.item;
+        atomicAdd(&p.cnt->stat[7], 1u);
+        atomicAdd(&p.cnt->cells[7], (unsigned long long)L.cells);
+        active = false;
       }
     }
   }
@@ -1783,7 +1798,7 @@ dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/30, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
-    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0};
+    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0, /*narrow_split_d=*/0};
 
 struct DeviceInfo {
   bool ready = false;
@@ -1800,7 +1815,7 @@ std::mutex g_dev_mu;
 DeviceInfo g_dev[64];
 
 bool g_timing = false;
-cudaEvent_t g_ev[8] = {};
+cudaEvent_t g_ev[10] = {};
 // Per-warp clock of one launch per batch (dibella_enable_warp_clock): which
 // launch (0 none, 1 narrow, 2 first wide, 3 mid, 4 wide on the escalations)
 // and how many warps the last clocked launch ran.
@@ -1934,6 +1949,7 @@ int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_band_cap != 32 && s.narrow_band_cap != 48 && s.narrow_band_cap != 64) return DIBELLA_EINVAL;
   if (s.mid_band_cap != 0 && s.mid_band_cap != 128 && s.mid_band_cap != 192 && s.mid_band_cap != 256)
     return DIBELLA_EINVAL;
+  if (s.narrow_split_d < 0) return DIBELLA_EINVAL;
   if (s.wide_slots != 0 && s.wide_slots != 8 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32)
     return DIBELLA_EINVAL;
   if (s.wide_slots == 8 && s.wide_group_lanes != 0 && s.wide_group_lanes != 32) return DIBELLA_EINVAL;
@@ -2104,9 +2120,14 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
 //                      rung hands a short queue on unextended)
 //   CTA form           on Smem          (outgrown -> Global)
 //   global form        on Global
+// With narrow_split_d > 0 the narrow form runs twice: the first pass stops
+// every extension at antidiagonal narrow_split_d and queues the unfinished
+// ones on Long, which the second pass runs from the origin (so that lanes with
+// long extensions are not interleaved with the refills of short ones).
 // Every launch whose queue is empty returns at once.  Phase events: 2 after
-// the narrow launch, 3 after the first wide launch, 4 after the mid form (at
-// once when there is none), 5 after the wide launch on the escalations, 6
+// the (first) narrow launch, 3 after the second narrow pass (at once when
+// there is none), 4 after the first wide launch, 5 after the mid form (at
+// once when there is none), 6 after the wide launch on the escalations, 7
 // after the ladder, CTA and global launches.
 int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, ExtendParams ep,
                       int* const q[kNumQ], cudaStream_t st) {
@@ -2137,9 +2158,20 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.narrow_cells_idx = 0;
   ep.narrow_esc_stat = 2;
   ep.wclock = clock_for(1, D.sms * nb * kWarpsPerBlock, st);
+  ep.narrow_max_d = sch.narrow_split_d;
+  ep.long_q = q[kQLong];
   if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
   ep.wclock = nullptr;
+  ep.narrow_max_d = 0;
   record(st, 2);
+  if (sch.narrow_split_d > 0) {  // second pass: the long extensions, from the origin
+    ep.narrow_q = q[kQLong];
+    ep.narrow_q_id = kQLong;
+    ep.wclock = clock_for(5, D.sms * nb * kWarpsPerBlock, st);
+    if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch 2");
+    ep.wclock = nullptr;
+  }
+  record(st, 3);
 
   // The configured wide form; its escalations climb the ladder.
   ep.narrow_q = nullptr;
@@ -2152,7 +2184,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wclock = clock_for(2, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
   ep.wclock = nullptr;
-  record(st, 3);
+  record(st, 4);
   int esc_in = kQEsc1;
   if (sch.mid_band_cap > 0 && narrow_kind(xdrop) == 1) {
     const int wide_esc_q = ep.esc_q_id;
@@ -2171,14 +2203,14 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     ep.esc_q_id = wide_esc_q;
     esc_in = kQEsc2;
   }
-  record(st, 4);
+  record(st, 5);
   ep.wide_q = q[esc_in];
   ep.wide_q_id = esc_in;
   ep.cells_idx = 4;
   ep.wclock = clock_for(4, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
   ep.wclock = nullptr;
-  record(st, 5);
+  record(st, 6);
   ep.cells_idx = 5;
   for (int r = 0; r < n_rungs; ++r) {
     dibella_schedule_t up = sch;
@@ -2210,7 +2242,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   global_kernel<<<kGlobalWarps / kWarpsPerBlock, kBlockThreads, 0, st>>>(ep);
   ++g_launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "global launch");
-  record(st, 6);
+  record(st, 7);
   return DIBELLA_OK;
 }
 
@@ -2284,7 +2316,7 @@ constexpr size_t kNoAllocBytes =
     up256(sizeof(Counters)) + up256(sizeof(Item) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(ExtOut) * 2 * kNoAllocMaxPairs) + kNumQ * up256(sizeof(int) * 2 * kNoAllocMaxPairs) +
     up256(sizeof(int) * 3 * (size_t)kNoAllocBandCap * kGlobalWarps);
-static_assert(kNoAllocBytes == 9437696, "the size stated in include/dibella.h must follow the layout");
+static_assert(kNoAllocBytes == 9568768, "the size stated in include/dibella.h must follow the layout");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of the scratch array on the current device.
@@ -2389,12 +2421,14 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   ep.cells_idx = 1;
   ep.wclock = nullptr;
   ep.q_cap = 2 * n_pairs;
+  ep.narrow_max_d = 0;
+  ep.long_q = nullptr;
   int* q[kNumQ];
   for (int i = 0; i < kNumQ; ++i) q[i] = (int*)(ws + L.queue[i]);
   rc = launch_extensions(*D, sch, scoring.xdrop, ep, q, st);
   if (rc != DIBELLA_OK) return rc;
   rc = finish(read_lengths, pairs, n_pairs, k, results, ep.ext, st);
-  record(st, 7);
+  record(st, 8);
   return rc;
 }
 
@@ -2622,6 +2656,17 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       rc = consider(c);
     }
   }
+  // Stage 1c: the split of the narrow launch (none, or a first pass of 64, 128 or 256 antidiagonals).
+  {
+    const dibella_schedule_t base1c = cur;
+    const int splits[4] = {0, 64, 128, 256};
+    for (int si = 0; si < 4 && rc == DIBELLA_OK; ++si) {
+      if (splits[si] == base1c.narrow_split_d) continue;
+      dibella_schedule_t c = base1c;
+      c.narrow_split_d = splits[si];
+      rc = consider(c);
+    }
+  }
   // Stage 2: lanes per extension (warp or 16/8-lane groups) x register slots of the wide form.
   {
     const dibella_schedule_t base2 = cur;
@@ -2663,7 +2708,7 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
 
 int dibella_enable_phase_timing(int enable) {
   if (enable) {
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 10; ++i) {
       if (g_ev[i] != nullptr) continue;
       cudaError_t e = cudaEventCreate(&g_ev[i]);
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -2696,11 +2741,11 @@ int dibella_batch_counters(const void* workspace, void* stream, int64_t* out, in
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counters");
   e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  const int64_t v[15] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
+  const int64_t v[16] = {c.stat[0], c.stat[1], c.stat[2], c.stat[3], c.stat[4], c.stat[5],
                          (int64_t)c.cells[0], (int64_t)(c.cells[1] + c.cells[4] + c.cells[5]),
                          (int64_t)c.cells[2], (int64_t)c.cells[3], (int64_t)c.cells[4],
-                         (int64_t)c.cells[5], (int64_t)c.cells[6], c.stat[6], (int64_t)c.cells[7]};
-  int n = std::min(n_max, 15);
+                         (int64_t)c.cells[5], (int64_t)c.cells[6], c.stat[6], (int64_t)c.cells[7], c.stat[7]};
+  int n = std::min(n_max, 16);
   for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
 }
@@ -2728,7 +2773,7 @@ int dibella_bounds_check(int64_t* out, int reset) {
 }
 
 int dibella_enable_warp_clock(int launch) {
-  if (launch < 0 || launch > 4) return DIBELLA_EINVAL;
+  if (launch < 0 || launch > 5) return DIBELLA_EINVAL;
   g_clock_launch = launch;
   g_clocked_warps = 0;
   return DIBELLA_OK;

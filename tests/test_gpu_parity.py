@@ -34,7 +34,8 @@ def test_c1_all_pairs(c1, X):
     assert ((got["status"] & 4) != 0).sum() == len(workloads.pair_groups(c1.pairs)) - 1
 
 
-@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "mid128", "mid192", "mid256", "nomid",
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "split16", "split64", "mid128", "mid192",
+                                  "mid256", "nomid",
                                   "packed8", "packed16", "packed24", "packed32",
                                   "int16", "int32", "grp16x16", "grp16x24", "grp16x32", "grp8x16", "grp8x24"])
 @pytest.mark.parametrize("X", [0, 3, 7, 25])
@@ -50,6 +51,9 @@ def test_every_kernel_form_matches(c1, form, X):
     elif form.startswith("mid"):
         # every extension through the 32-cell narrow form, its escalations through the mid form
         sched = schedule(narrow_band_cap=32, mid_band_cap=int(form[3:]), **NARROW_ALL)
+    elif form.startswith("split"):
+        # the narrow form in two passes, the first stopping at antidiagonal 16 or 64
+        sched = schedule(narrow_split_d=int(form[5:]), **NARROW_ALL)
     elif form == "nomid":
         sched = schedule(narrow_band_cap=32, mid_band_cap=0, **NARROW_ALL)
     else:
@@ -116,7 +120,7 @@ def test_fuzz_medium(scoring):
         exp = oracle_align(ascii, offs, pairs, k, sc)
         for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL),
                       schedule(narrow_band_cap=32, mid_band_cap=128, **NARROW_ALL),
-                      schedule(mid_band_cap=0, **NARROW_ALL),
+                      schedule(mid_band_cap=0, **NARROW_ALL), schedule(narrow_split_d=40, **NARROW_ALL),
                       schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, wide_group_lanes=32, **WIDE_ALL),
                       schedule(wide_group_lanes=16, **WIDE_ALL), schedule(wide_group_lanes=8, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
@@ -235,6 +239,13 @@ def test_counters_report_routing(c1):
     total = lambda d: sum(d[f] for f in ("cells_narrow", "cells_wide", "cells_smem", "cells_global", "cells_mid"))
     # escalated extensions restart, so the finished cells of both runs agree
     assert total(c2) == total(c)
+    # the narrow form in two passes: one launch more, the long extensions run again from the origin
+    al.align(c1.pairs, dib.Scoring(1, -1, -1, 25), sched=schedule(narrow_band_cap=32, narrow_split_d=50,
+                                                                  **NARROW_ALL))
+    assert dib.dibella_last_launch_count() == 14
+    c3 = dib.dibella_batch_counters(al.workspace)
+    assert c3["narrow_second_pass"] > 0 and c3["cells_restarted"] > c["cells_restarted"]
+    assert total(c3) == total(c)
 
 
 def test_c2_full_size_sampled():
