@@ -73,6 +73,10 @@ def parse():
     # profiling / exploration knobs (the defaults are the benchmark)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--xdrops", default=",".join(str(x) for x in XDROPS))
+    ap.add_argument("--read-ranges", default=None,
+                    help="lo:hi,lo:hi,...: align only the candidate pairs whose read_a lies in these read-id ranges, "
+                         "from the generator's index restricted to them (the whole read store stays resident; "
+                         "this is how a batch on the full 100 Mb repeat genome is run without its whole index)")
     ap.add_argument("--sample-pairs", type=int, default=0,
                     help="align a seeded sample of this many candidate pairs instead of all")
     ap.add_argument("--schedule", default=None, help="JSON dict: an explicit schedule (default schedule's fields "
@@ -142,7 +146,7 @@ NCU_TRAFFIC = {
 
 
 def traffic_for(workload, args, X, launch):
-    if args.schedule or args.sample_pairs:
+    if args.schedule or args.sample_pairs or args.default_schedule or args.read_ranges:
         return None
     return NCU_TRAFFIC.get((workload, X, launch))
 
@@ -774,7 +778,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     XD = args.xdrops
-    w = workloads.generate(args.workload)
+    if args.read_ranges:
+        rr = [tuple(int(v) for v in r.split(":")) for r in args.read_ranges.split(",")]
+        w = workloads.generate(args.workload, pairs_mode=workloads.PAIRS_RANGES, read_ranges=rr, cache=False)
+    else:
+        w = workloads.generate(args.workload)
     pairs = w.pairs
     if args.sample_pairs:
         pairs = workloads.sample_pair_groups(pairs, args.sample_pairs, seed=29)
@@ -985,7 +993,8 @@ def main():
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": w.name + (" (sample of %d pairs)" % n_cand if args.sample_pairs else ""),
+        "config": {"workload": w.name + (" (sample of %d pairs)" % n_cand if args.sample_pairs else "")
+                               + (" (read_a in %s)" % args.read_ranges if args.read_ranges else ""),
                    "genome_bp": w.params["genome_len"], "coverage": w.params["coverage"],
                    "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n_seeds,
                    "xdrop": list(XD), "scoring": "+1/-1/-1", "k": K,
