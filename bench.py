@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mono", action="store_true", help="skip the score-versus-X violation count")
+    ap.add_argument("--no-balance", action="store_true", help="skip the per-warp queue-balance batches")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split the one batch across ranks by cost key (whole candidate pairs) instead of "
                          "aligning a replica per rank")
@@ -889,7 +890,7 @@ def main():
     # time measured from the launch's first warp start (the analogue of the
     # paper's max/avg rank time, Sec. 9 and Fig. 8).
     balance = {}
-    for X in XD:
+    for X in (() if args.no_balance else XD):
         balance[str(X)] = {}
         for name, which in dib.WARP_CLOCK_LAUNCHES.items():
             dib.dibella_enable_warp_clock(which)
