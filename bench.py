@@ -384,9 +384,9 @@ def mode_tune(args):
 def mode_traceback(args):
     """Traceback of accepted overlaps (the edits of each best alignment,
     diBELLA Sec. 1-2): the best seed of every E. coli-sized candidate pair whose
-    X = 25 alignment spans at least 2 kb of A at a score of at least 0.4 per
-    column of A (true overlaps; pairs that share a k-mer by chance score near
-    0 per column), a seeded sample of them, aligned again with every cell's
+    X = 25 alignment spans at least 2 kb of A at a score of at least 0.2 per
+    column of A (true overlaps score about 0.4 per column at 15% error per read;
+    pairs that share a k-mer by chance score near 0), a seeded sample of them, aligned again with every cell's
     move kept and walked back on the GPU (dibella_xdrop_traceback, a warp per
     seed).  value = seeds traced per second; the cell rate and the bytes of
     the move stream per cell go with it."""
@@ -399,7 +399,7 @@ def mode_traceback(args):
     al = dib.Aligner(store, len(w.pairs), k=K, device=dev)
     res = al.align(w.pairs, dib.Scoring(1, -1, -1, X))
     span = res["end_a"].astype(np.int64) - res["begin_a"].astype(np.int64)
-    acc = np.flatnonzero(((res["status"] & 4) != 0) & (span >= 2000) & (res["score"] >= 0.4 * span))
+    acc = np.flatnonzero(((res["status"] & 4) != 0) & (span >= 2000) & (res["score"] >= 0.2 * span))
     rng = np.random.default_rng(31)
     pick = np.sort(rng.choice(acc, size=min(args.trace_seeds, len(acc)), replace=False))
     seeds = w.pairs[pick]
@@ -440,7 +440,7 @@ def mode_traceback(args):
         "metric": "traced seeds/s", "mode": "traceback", "value": n / (ms * 1e-3), "unit": "seeds/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
         "gcups": cells / (ms * 1e-3) / 1e9, "ms": ms,
-        "config": {"workload": WORKLOAD + " accepted overlaps (best seed, >= 2 kb of A, score >= 0.4 per column)",
+        "config": {"workload": WORKLOAD + " accepted overlaps (best seed, >= 2 kb of A, score >= 0.2 per column)",
                    "accepted": int(len(acc)), "seeds": n, "xdrop": X, "warps": lanes,
                    "moves_words_per_warp": moves_words, "ops_per_seed": ops_per_seed, "steps": args.steps},
         "cells": cells, "runs": int(nops[nops > 0].sum()), "seeds_complete": int((nops > 0).sum()),
