@@ -169,6 +169,8 @@ typedef struct {
   int32_t mid_band_cap;           /* mid form: 0 (none), 128, 192 or 256      */
   int32_t narrow_split_d;         /* > 0: narrow form in two passes, the      */
                                   /* first stopping at this antidiagonal      */
+  int32_t narrow_unroll;          /* narrow form: cells per unrolled group of */
+                                  /* its band walk, 4, 8 or 16 (0 = 16)       */
 } dibella_schedule_t;
 
 /* The schedule used when a call passes NULL.  set() validates (EINVAL). */
@@ -441,7 +443,8 @@ int dibella_xdrop_traceback(const uint32_t* packed_words, const int64_t* read_wo
  * *best_out (median of `repeats` timed runs each, CUDA events on `stream`).
  * The search is staged: routing threshold between the one-thread and the
  * wide forms x per-thread band chunk (32/48/64), then the mid form's band
- * (none/128/192/256), then lanes per extension
+ * (none/128/192/256), the split of the narrow form (none/64/128/256
+ * antidiagonals) and its cell groups (4/8/16), then lanes per extension
  * (32/16/8) x register slots (16/24/32) of the wide form, then resident
  * blocks per SM, then length-bucket bounds; each stage keeps the best so
  * far.  Same arguments as

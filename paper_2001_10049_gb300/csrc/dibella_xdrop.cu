@@ -782,10 +782,15 @@ __device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, T* wbas
 }
 
 // One antidiagonal for one lane.  Returns 1 when the extension finished,
-// 2 when its band outgrew the lane's storage, 0 otherwise.
-template <int WT, typename T>
+// 2 when its band outgrew the lane's storage, 0 otherwise.  The band is walked
+// in groups of U cells (unrolled, each cell guarded by the band's end): a lane
+// issues the instructions of every cell of its last group, so U = 16 wastes up
+// to 15 cell slots on a narrow band and U = 4 at most 3, for one loop step
+// per group.
+template <int WT, typename T, int U>
 __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words, const Scoring sc,
                            T* wbase, int lane) {
+  static_assert(U == 4 || U == 8 || U == 16, "groups of 4, 8 or 16 cells");
   constexpr int kD = NarrowCell<T>::kDead;
   const int d = L.d;
   const int lo = max(L.live_lo, d - L.n);
@@ -820,20 +825,23 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
     const uint32_t x = ~(wa ^ wb);
     const uint32_t mm = (x | (x >> 1)) & 0x55555555u;
     const int cnt = min(16, hi - i + 1);
-    T* p1 = &nslot<WT>(wbase, h1, i - f, lane);
-    T* p2 = &nslot<WT>(wbase, h2, i - f, lane);
+    for (int g = 0; g < cnt; g += U) {
+      T* p1 = &nslot<WT>(wbase, h1, i + g - f, lane);
+      T* p2 = &nslot<WT>(wbase, h2, i + g - f, lane);
+      const uint32_t mg = mm >> (2 * g);
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      if (t < cnt) {
-        const int lf = p1[t * 32];
-        const int dn = p2[t * 32];
-        const int sub = ((mm >> (2 * t)) & 1u) ? sc.S : sc.M;
-        int h = max(max(u, lf) + sc.G, dg + sub);
-        h = h >= thr ? h : kD;
-        p2[t * 32] = (T)h;
-        vmax = max(vmax, h);
-        u = lf;
-        dg = dn;
+      for (int t = 0; t < U; ++t) {
+        if (g + t < cnt) {
+          const int lf = p1[t * 32];
+          const int dn = p2[t * 32];
+          const int sub = ((mg >> (2 * t)) & 1u) ? sc.S : sc.M;
+          int h = max(max(u, lf) + sc.G, dg + sub);
+          h = h >= thr ? h : kD;
+          p2[t * 32] = (T)h;
+          vmax = max(vmax, h);
+          u = lf;
+          dg = dn;
+        }
       }
     }
   }
@@ -1467,7 +1475,7 @@ __global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
 // escalations, whose bands (about 100-200 cells for reads that share their
 // seed by chance) a lane walks for ~12 warp instructions per 32 cells, against
 // a fixed per-antidiagonal control cost for a whole warp per extension.
-template <int WT, typename T, int NW>
+template <int WT, typename T, int NW, int U>
 __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
   extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
@@ -1510,7 +1518,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
       continue;
     }
     if (active) {
-      const int r = narrow_step<WT, T>(L, p.words, p.sc, wbase, lane);
+      const int r = narrow_step<WT, T, U>(L, p.words, p.sc, wbase, lane);
       if (r == 1) {
         ExtOut o;
         o.best = L.best; o.i_end = L.bi; o.j_end = L.bj; o.status = 0; o.cells = L.cells;
@@ -1798,12 +1806,13 @@ dibella_schedule_t g_default_schedule = {
     /*narrow_max_xdrop=*/30, /*narrow_max_len=*/1 << 30, /*narrow_band_cap=*/48,
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
-    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0, /*narrow_split_d=*/0};
+    /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0, /*narrow_split_d=*/0,
+    /*narrow_unroll=*/0};
 
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
-  int narrow_blocks[2][3] = {};  // narrow_kernel<32/48/64, int | short> blocks per SM
+  int narrow_blocks[2][3][3] = {};  // narrow_kernel<32/48/64, int | short, ., 4/8/16-cell groups> blocks per SM
   int mid_blocks[3] = {};        // narrow_kernel<128/192/256, short, 1> (the mid form) blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
   int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
@@ -1908,23 +1917,35 @@ int device_info(DeviceInfo** out) {
     e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     int rc = DIBELLA_OK;
-    if ((rc = occupancy(&D.narrow_blocks[0][0], (const void*)narrow_kernel<32, int, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<32, int, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.narrow_blocks[0][1], (const void*)narrow_kernel<48, int, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<48, int, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.narrow_blocks[0][2], (const void*)narrow_kernel<64, int, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<64, int, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][0], (const void*)narrow_kernel<32, short, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<32, short, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][1], (const void*)narrow_kernel<48, short, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<48, short, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.narrow_blocks[1][2], (const void*)narrow_kernel<64, short, kWarpsPerBlock>, kBlockThreads,
-                        narrow_smem<64, short, kWarpsPerBlock>())) ||
-        (rc = occupancy(&D.mid_blocks[0], (const void*)narrow_kernel<128, short, 1>, 32,
+    if ((rc = occupancy(&D.narrow_blocks[0][0][2], (const void*)narrow_kernel<32, int, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<32, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][1][2], (const void*)narrow_kernel<48, int, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<48, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[0][2][2], (const void*)narrow_kernel<64, int, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<64, int, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0][0], (const void*)narrow_kernel<32, short, kWarpsPerBlock, 4>,
+                        kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1][0], (const void*)narrow_kernel<48, short, kWarpsPerBlock, 4>,
+                        kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2][0], (const void*)narrow_kernel<64, short, kWarpsPerBlock, 4>,
+                        kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0][1], (const void*)narrow_kernel<32, short, kWarpsPerBlock, 8>,
+                        kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1][1], (const void*)narrow_kernel<48, short, kWarpsPerBlock, 8>,
+                        kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2][1], (const void*)narrow_kernel<64, short, kWarpsPerBlock, 8>,
+                        kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0][2], (const void*)narrow_kernel<32, short, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1][2], (const void*)narrow_kernel<48, short, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2][2], (const void*)narrow_kernel<64, short, kWarpsPerBlock, 16>,
+                        kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.mid_blocks[0], (const void*)narrow_kernel<128, short, 1, 16>, 32,
                         narrow_smem<128, short, 1>())) ||
-        (rc = occupancy(&D.mid_blocks[1], (const void*)narrow_kernel<192, short, 1>, 32,
+        (rc = occupancy(&D.mid_blocks[1], (const void*)narrow_kernel<192, short, 1, 16>, 32,
                         narrow_smem<192, short, 1>())) ||
-        (rc = occupancy(&D.mid_blocks[2], (const void*)narrow_kernel<256, short, 1>, 32,
+        (rc = occupancy(&D.mid_blocks[2], (const void*)narrow_kernel<256, short, 1, 16>, 32,
                         narrow_smem<256, short, 1>())) ||
         (rc = occupancy(&D.reg_blocks[0], (const void*)wide_reg_kernel<16>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.reg_blocks[1], (const void*)wide_reg_kernel<32>, kBlockThreads, 0)) ||
@@ -1939,6 +1960,8 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.grp8_blocks[1], (const void*)wide_grp_kernel<8, 24>, kBlockThreads, 0)) ||
         (rc = occupancy(&D.cta_blocks, (const void*)wide_cta_kernel, kCtaThreads, kCtaSmemBytes)))
       return rc;
+    for (int w = 0; w < 3; ++w)  // the int32 rows come in 16-cell groups only
+      D.narrow_blocks[0][w][0] = D.narrow_blocks[0][w][1] = D.narrow_blocks[0][w][2];
     D.ready = true;
   }
   *out = &D;
@@ -1950,6 +1973,8 @@ int validate_schedule(const dibella_schedule_t& s) {
   if (s.mid_band_cap != 0 && s.mid_band_cap != 128 && s.mid_band_cap != 192 && s.mid_band_cap != 256)
     return DIBELLA_EINVAL;
   if (s.narrow_split_d < 0) return DIBELLA_EINVAL;
+  if (s.narrow_unroll != 0 && s.narrow_unroll != 4 && s.narrow_unroll != 8 && s.narrow_unroll != 16)
+    return DIBELLA_EINVAL;
   if (s.wide_slots != 0 && s.wide_slots != 8 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32)
     return DIBELLA_EINVAL;
   if (s.wide_slots == 8 && s.wide_group_lanes != 0 && s.wide_group_lanes != 32) return DIBELLA_EINVAL;
@@ -1997,21 +2022,39 @@ void record(cudaStream_t st, int idx) {
 // int16 narrow cells (relative scores) when X allows, else int32.
 inline int narrow_kind(int xdrop) { return xdrop <= kNarrow16MaxX ? 1 : 0; }
 
-cudaError_t launch_narrow(int wt, int xdrop, int grid, cudaStream_t st, const ExtendParams& ep) {
+// Index of a schedule's narrow cell group width (narrow_unroll 0 means 16).
+inline int unroll_index(int u) { return u == 4 ? 0 : (u == 8 ? 1 : 2); }
+
+template <int WT, int U>
+void launch_narrow16(int grid, cudaStream_t st, const ExtendParams& ep) {
+  narrow_kernel<WT, short, kWarpsPerBlock, U><<<grid, kBlockThreads, narrow_smem<WT, short, kWarpsPerBlock>(), st>>>(ep);
+}
+
+template <int WT>
+void launch_narrow16_u(int unroll, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (unroll == 4)
+    launch_narrow16<WT, 4>(grid, st, ep);
+  else if (unroll == 8)
+    launch_narrow16<WT, 8>(grid, st, ep);
+  else
+    launch_narrow16<WT, 16>(grid, st, ep);
+}
+
+cudaError_t launch_narrow(int wt, int unroll, int xdrop, int grid, cudaStream_t st, const ExtendParams& ep) {
   if (narrow_kind(xdrop)) {
     if (wt == 32)
-      narrow_kernel<32, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>(), st>>>(ep);
+      launch_narrow16_u<32>(unroll, grid, st, ep);
     else if (wt == 48)
-      narrow_kernel<48, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>(), st>>>(ep);
+      launch_narrow16_u<48>(unroll, grid, st, ep);
     else
-      narrow_kernel<64, short, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>(), st>>>(ep);
+      launch_narrow16_u<64>(unroll, grid, st, ep);
   } else {
     if (wt == 32)
-      narrow_kernel<32, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<32, int, kWarpsPerBlock>(), st>>>(ep);
+      narrow_kernel<32, int, kWarpsPerBlock, 16><<<grid, kBlockThreads, narrow_smem<32, int, kWarpsPerBlock>(), st>>>(ep);
     else if (wt == 48)
-      narrow_kernel<48, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<48, int, kWarpsPerBlock>(), st>>>(ep);
+      narrow_kernel<48, int, kWarpsPerBlock, 16><<<grid, kBlockThreads, narrow_smem<48, int, kWarpsPerBlock>(), st>>>(ep);
     else
-      narrow_kernel<64, int, kWarpsPerBlock><<<grid, kBlockThreads, narrow_smem<64, int, kWarpsPerBlock>(), st>>>(ep);
+      narrow_kernel<64, int, kWarpsPerBlock, 16><<<grid, kBlockThreads, narrow_smem<64, int, kWarpsPerBlock>(), st>>>(ep);
   }
   ++g_launches;
   return cudaGetLastError();
@@ -2022,11 +2065,11 @@ cudaError_t launch_mid(const DeviceInfo& D, int wt, cudaStream_t st, const Exten
   const int vi = wt == 128 ? 0 : (wt == 192 ? 1 : 2);
   const int grid = D.sms * D.mid_blocks[vi];
   if (wt == 128)
-    narrow_kernel<128, short, 1><<<grid, 32, narrow_smem<128, short, 1>(), st>>>(ep);
+    narrow_kernel<128, short, 1, 16><<<grid, 32, narrow_smem<128, short, 1>(), st>>>(ep);
   else if (wt == 192)
-    narrow_kernel<192, short, 1><<<grid, 32, narrow_smem<192, short, 1>(), st>>>(ep);
+    narrow_kernel<192, short, 1, 16><<<grid, 32, narrow_smem<192, short, 1>(), st>>>(ep);
   else
-    narrow_kernel<256, short, 1><<<grid, 32, narrow_smem<256, short, 1>(), st>>>(ep);
+    narrow_kernel<256, short, 1, 16><<<grid, 32, narrow_smem<256, short, 1>(), st>>>(ep);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -2146,7 +2189,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   auto rung_queue = [&](int slots) { return kQLadder + (slots / 8 - 1); };  // 8..32 -> 3..6
   const int wt = sch.narrow_band_cap;
   const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
-  int nb = D.narrow_blocks[narrow_kind(xdrop)][vi];
+  const int unroll = sch.narrow_unroll == 0 ? 16 : sch.narrow_unroll;
+  int nb = D.narrow_blocks[narrow_kind(xdrop)][vi][unroll_index(unroll)];
   if (sch.narrow_blocks_per_sm > 0) nb = std::min(nb, sch.narrow_blocks_per_sm);
   cudaError_t e;
 
@@ -2160,7 +2204,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wclock = clock_for(1, D.sms * nb * kWarpsPerBlock, st);
   ep.narrow_max_d = sch.narrow_split_d;
   ep.long_q = q[kQLong];
-  if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
+  if ((e = launch_narrow(wt, unroll, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
   ep.wclock = nullptr;
   ep.narrow_max_d = 0;
   record(st, 2);
@@ -2168,7 +2212,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     ep.narrow_q = q[kQLong];
     ep.narrow_q_id = kQLong;
     ep.wclock = clock_for(5, D.sms * nb * kWarpsPerBlock, st);
-    if ((e = launch_narrow(wt, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch 2");
+    if ((e = launch_narrow(wt, unroll, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch 2");
     ep.wclock = nullptr;
   }
   record(st, 3);
@@ -2394,7 +2438,9 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
   if (sched == nullptr) {
     const int wt = sch.narrow_band_cap;
     const long long narrow_lanes =
-        (long long)D->sms * D->narrow_blocks[narrow_kind(scoring.xdrop)][wt == 32 ? 0 : (wt == 48 ? 1 : 2)] *
+        (long long)D->sms *
+        D->narrow_blocks[narrow_kind(scoring.xdrop)][wt == 32 ? 0 : (wt == 48 ? 1 : 2)]
+                        [unroll_index(sch.narrow_unroll == 0 ? 16 : sch.narrow_unroll)] *
         kBlockThreads;
     if (2 * 2 * n_pairs < 3 * narrow_lanes) sch.narrow_max_xdrop = -1;
     else if (scoring.xdrop > 10)
@@ -2664,6 +2710,17 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       if (splits[si] == base1c.narrow_split_d) continue;
       dibella_schedule_t c = base1c;
       c.narrow_split_d = splits[si];
+      rc = consider(c);
+    }
+  }
+  // Stage 1d: the narrow form's cell groups (4, 8 or 16 cells).
+  {
+    const dibella_schedule_t base1d = cur;
+    const int unrolls[3] = {4, 8, 16};
+    for (int ui = 0; ui < 3 && rc == DIBELLA_OK; ++ui) {
+      if (unrolls[ui] == (base1d.narrow_unroll == 0 ? 16 : base1d.narrow_unroll)) continue;
+      dibella_schedule_t c = base1d;
+      c.narrow_unroll = unrolls[ui];
       rc = consider(c);
     }
   }
