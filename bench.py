@@ -137,13 +137,14 @@ def max_over_ranks(value: float, device=None) -> float:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel, from a one-pass ncu capture of this bench's default
-# command (profiles/ names the file and the command).  Keyed by workload, X and
-# launch; valid only for the default schedule and the kernels it was taken on.
-NCU_TRAFFIC = {
-    # profiles/launch_list_c2_ecoli_bench.md: mean of the four X = 25 launches
-    ("c2_ecoli", 25, "wide form on the narrow escalations"): 609061568,
-}
+# the dominant kernel, keyed by workload, X and launch, from an ncu capture that
+# the pool's rules allow (one kernel, 1-3 launches, a small case) scaled to a
+# full launch by the cells it processes -- only where traffic grows in
+# proportion.  On the E. coli-sized batch it does not (the 70 MB read store
+# stays in L2 at full size, a sample's traffic is mostly its first touches), so
+# no figure is kept and `traffic` is null; profiles/ holds the small-case bytes
+# per cell.
+NCU_TRAFFIC = {}
 
 
 def traffic_for(workload, args, X, launch):
