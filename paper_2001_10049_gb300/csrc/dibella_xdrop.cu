@@ -185,14 +185,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Start and end of this warp's work in a clocked launch (lane 0 writes).
-__device__ __forceinline__ void warp_clock_out(unsigned long long* wclock, unsigned long long t0) {
+// Start (at = 0) or end (at = 1) of this warp's work in a clocked launch,
+// written at once by lane 0 so that no timer value stays live in registers
+// across the persistent loop.
+__device__ __forceinline__ void warp_clock(unsigned long long* wclock, int at) {
   if (wclock == nullptr || (threadIdx.x & 31) != 0) return;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w < kMaxClockedWarps) {
-    wclock[2 * w] = t0;
-    wclock[2 * w + 1] = global_ns();
-  }
+  if (w < kMaxClockedWarps) wclock[2 * w + at] = global_ns();
 }
 
 __device__ __forceinline__ unsigned pop_warp(Counters* cnt, int q) {
@@ -876,7 +875,7 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
 template <int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
-  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
+  warp_clock(p.wclock, 0);
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const bool fwd = tail <= p.forward_max;
   for (;;) {
@@ -904,7 +903,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
     }
     __syncwarp();
   }
-  warp_clock_out(p.wclock, wt0);
+  warp_clock(p.wclock, 1);
 }
 
 // Packed form, one warp per extension (routed here only when X <= kPackedMaxX).
@@ -916,7 +915,7 @@ template <int NC>
 __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (NC == 24 ? 4 : 1)))
     wide_pk_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
-  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
+  warp_clock(p.wclock, 0);
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const bool fwd = NC > 8 && tail <= p.forward_max;  // 8 slots is never a ladder rung
   for (;;) {
@@ -944,7 +943,7 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
     }
     __syncwarp();
   }
-  warp_clock_out(p.wclock, wt0);
+  warp_clock(p.wclock, 1);
 }
 
 // Grouped packed form: a warp runs NG = 32/GL extensions at once, GL lanes
@@ -982,7 +981,7 @@ __device__ __forceinline__ int grp_reduce_min(int v, int g) {
 template <int GL, int NC>
 __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p) {
   static_assert(GL == 8 || GL == 16, "group of 8 or 16 lanes");
-  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
+  warp_clock(p.wclock, 0);
   static_assert(NC % 8 == 0 && NC >= 8 && NC <= 32, "slots come in words of 8");
   constexpr int NW = NC / 8;
   constexpr int NG = 32 / GL;
@@ -1070,7 +1069,7 @@ __global__ void __launch_bounds__(kBlockThreads) wide_grp_kernel(ExtendParams p)
     }
     if (!__any_sync(kFull, active)) {
       if (__all_sync(kFull, exhausted)) {
-        warp_clock_out(p.wclock, wt0);
+        warp_clock(p.wclock, 1);
         break;
       }
       continue;
@@ -1480,7 +1479,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
   extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
   T* wbase = reinterpret_cast<T*>(smem_words) + (threadIdx.x >> 5) * (2 * WT * 32);
-  const unsigned long long wt0 = p.wclock ? global_ns() : 0ull;
+  warp_clock(p.wclock, 0);
   const unsigned ntail = *((volatile unsigned*)&p.cnt->tail[p.narrow_q_id]);
   NarrowLane<WT> L;
   bool active = false, exhausted = false;
@@ -1512,7 +1511,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
     }
     if (!__any_sync(kFull, active)) {
       if (__all_sync(kFull, exhausted)) {
-        warp_clock_out(p.wclock, wt0);
+        warp_clock(p.wclock, 1);
         break;
       }
       continue;
