@@ -409,7 +409,7 @@ def mode_traceback(args):
     moves_words = 1 << 20
     tal = dib.Aligner(store, n, k=K, device=dev)
     tal.upload_pairs(seeds)
-    ops_per_seed = 4096
+    ops_per_seed = 16384  # runs of a 60 kb overlap at 15% error per read stay below this
     ops = torch.zeros((n, ops_per_seed), dtype=torch.int32, device=dev)
     n_ops = torch.zeros(n, dtype=torch.int32, device=dev)
     ws_bytes = dib.dibella_traceback_workspace_bytes(lanes, store.max_len, moves_words)

@@ -565,7 +565,11 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
       const int r = b_rel - d + 64 * c0;  // lane 0, low cell of slot 1: store index b_lo - d + 64*c0
       if ((r >> 4) != bq_idx) {  // r falls by one per antidiagonal: one load per 16
         bq_idx = r >> 4;
+#ifdef DIBELLA_BOUNDS_CHECK
         bq = ldg_word(words, (long long)(bwords - words) + bq_idx);
+#else
+        bq = __ldg(bwords + bq_idx);
+#endif
       }
       const int bfresh = (int)((bq >> ((unsigned)(r & 15) * 2u)) & 3u);
       unsigned prev_top = 0;
