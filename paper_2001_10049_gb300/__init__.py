@@ -59,7 +59,8 @@ class Schedule(ctypes.Structure):
                 ("wide_blocks_per_sm", ctypes.c_int32),
                 ("narrow_blocks_per_sm", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
                 ("bucket_bounds", ctypes.c_int32 * MAX_BUCKETS), ("mid_band_cap", ctypes.c_int32),
-                ("narrow_split_d", ctypes.c_int32), ("narrow_unroll", ctypes.c_int32)]
+                ("narrow_split_d", ctypes.c_int32), ("narrow_unroll", ctypes.c_int32),
+                ("narrow_track", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"narrow_max_xdrop": self.narrow_max_xdrop, "narrow_max_len": self.narrow_max_len,
@@ -69,7 +70,7 @@ class Schedule(ctypes.Structure):
                 "narrow_blocks_per_sm": self.narrow_blocks_per_sm, "n_buckets": self.n_buckets,
                 "bucket_bounds": list(self.bucket_bounds)[: max(0, self.n_buckets - 1)],
                 "mid_band_cap": self.mid_band_cap, "narrow_split_d": self.narrow_split_d,
-                "narrow_unroll": self.narrow_unroll}
+                "narrow_unroll": self.narrow_unroll, "narrow_track": self.narrow_track}
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
@@ -81,6 +82,7 @@ class Schedule(ctypes.Structure):
         s.mid_band_cap = int(d.get("mid_band_cap", 0))
         s.narrow_split_d = int(d.get("narrow_split_d", 0))
         s.narrow_unroll = int(d.get("narrow_unroll", 0))
+        s.narrow_track = int(d.get("narrow_track", 0))
         bounds = list(d.get("bucket_bounds", []))
         for b in range(MAX_BUCKETS):
             s.bucket_bounds[b] = int(bounds[b]) if b < len(bounds) else 0

@@ -789,8 +789,11 @@ __device__ void narrow_init(NarrowLane<WT>& L, const Item& it, int item, T* wbas
 // in groups of U cells (unrolled, each cell guarded by the band's end): a lane
 // issues the instructions of every cell of its last group, so U = 16 wastes up
 // to 15 cell slots on a narrow band and U = 4 at most 3, for one loop step
-// per group.
-template <int WT, typename T, int U>
+// per group.  With TRACK the first and last live cell and the first cell of
+// the maximum are kept in registers while the band is walked (selects on every
+// lane), instead of being found afterwards by scans of the new row whose
+// lengths differ from lane to lane.
+template <int WT, typename T, int U, bool TRACK>
 __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words, const Scoring sc,
                            T* wbase, int lane) {
   static_assert(U == 4 || U == 8 || U == 16, "groups of 4, 8 or 16 cells");
@@ -821,6 +824,7 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
   int u = nslot<WT>(wbase, h1, lo - 1 - f, lane);
   int dg = nslot<WT>(wbase, h2, lo - 1 - f, lane);
   int vmax = kD;
+  int tr_first = INT32_MAX, tr_last = -1, tr_best = -1;  // TRACK: first / last live cell, first maximum
   const long long abase = L.a0 - 1, bbase = L.b0 + 1 - d;
   for (int i = lo; i <= hi; i += 16) {
     const uint32_t wa = base_window(words, abase + i);
@@ -841,6 +845,13 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
           int h = max(max(u, lf) + sc.G, dg + sub);
           h = h >= thr ? h : kD;
           p2[t * 32] = (T)h;
+          if (TRACK) {
+            const int ii = i + g + t;
+            const bool lv = h != kD;
+            tr_first = min(tr_first, lv ? ii : INT32_MAX);
+            tr_last = lv ? ii : tr_last;
+            tr_best = h > vmax ? ii : tr_best;  // strictly larger: the smallest i keeps a tie
+          }
           vmax = max(vmax, h);
           u = lf;
           dg = dn;
@@ -853,13 +864,19 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
   L.cells += hi - lo + 1;
   L.h1 = h2;
   if (vmax == kD) return 1;
-  int llo = lo;
-  while ((int)nslot<WT>(wbase, h2, llo - f, lane) == kD) ++llo;
-  int lhi = hi;
-  while ((int)nslot<WT>(wbase, h2, lhi - f, lane) == kD) --lhi;
+  int llo = tr_first, lhi = tr_last;
+  if (!TRACK) {
+    llo = lo;
+    while ((int)nslot<WT>(wbase, h2, llo - f, lane) == kD) ++llo;
+    lhi = hi;
+    while ((int)nslot<WT>(wbase, h2, lhi - f, lane) == kD) --lhi;
+  }
   if (vmax + L.rb > L.best) {
-    int b = llo;
-    while ((int)nslot<WT>(wbase, h2, b - f, lane) != vmax) ++b;
+    int b = tr_best;
+    if (!TRACK) {
+      b = llo;
+      while ((int)nslot<WT>(wbase, h2, b - f, lane) != vmax) ++b;
+    }
     L.best = vmax + L.rb;
     L.bi = b;
     L.bj = d - b;
@@ -1478,7 +1495,7 @@ __global__ void __launch_bounds__(kCtaThreads) wide_cta_kernel(ExtendParams p) {
 // escalations, whose bands (about 100-200 cells for reads that share their
 // seed by chance) a lane walks for ~12 warp instructions per 32 cells, against
 // a fixed per-antidiagonal control cost for a whole warp per extension.
-template <int WT, typename T, int NW, int U>
+template <int WT, typename T, int NW, int U, bool TRACK = false>
 __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
   extern __shared__ int smem_words[];
   const int lane = threadIdx.x & 31;
@@ -1521,7 +1538,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(ExtendParams p) {
       continue;
     }
     if (active) {
-      const int r = narrow_step<WT, T, U>(L, p.words, p.sc, wbase, lane);
+      const int r = narrow_step<WT, T, U, TRACK>(L, p.words, p.sc, wbase, lane);
       if (r == 1) {
         ExtOut o;
         o.best = L.best; o.i_end = L.bi; o.j_end = L.bj; o.status = 0; o.cells = L.cells;
@@ -1810,12 +1827,12 @@ dibella_schedule_t g_default_schedule = {
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
     /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0, /*narrow_split_d=*/0,
-    /*narrow_unroll=*/0};
+    /*narrow_unroll=*/0, /*narrow_track=*/0};
 
 struct DeviceInfo {
   bool ready = false;
   int sms = 0;
-  int narrow_blocks[2][3][3] = {};  // narrow_kernel<32/48/64, int | short, ., 4/8/16-cell groups> blocks per SM
+  int narrow_blocks[2][3][4] = {};  // narrow_kernel<32/48/64, int | short, ., 4/8/16 groups | tracked> per SM
   int mid_blocks[3] = {};        // narrow_kernel<128/192/256, short, 1> (the mid form) blocks per SM
   int reg_blocks[2] = {0, 0};        // wide_reg_kernel<16/32> blocks per SM
   int pk_blocks[4] = {0, 0, 0, 0};   // wide_pk_kernel<16/24/32/8> blocks per SM
@@ -1944,6 +1961,12 @@ int device_info(DeviceInfo** out) {
                         kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>())) ||
         (rc = occupancy(&D.narrow_blocks[1][2][2], (const void*)narrow_kernel<64, short, kWarpsPerBlock, 16>,
                         kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][0][3], (const void*)narrow_kernel<32, short, kWarpsPerBlock, 16, true>,
+                        kBlockThreads, narrow_smem<32, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][1][3], (const void*)narrow_kernel<48, short, kWarpsPerBlock, 16, true>,
+                        kBlockThreads, narrow_smem<48, short, kWarpsPerBlock>())) ||
+        (rc = occupancy(&D.narrow_blocks[1][2][3], (const void*)narrow_kernel<64, short, kWarpsPerBlock, 16, true>,
+                        kBlockThreads, narrow_smem<64, short, kWarpsPerBlock>())) ||
         (rc = occupancy(&D.mid_blocks[0], (const void*)narrow_kernel<128, short, 1, 16>, 32,
                         narrow_smem<128, short, 1>())) ||
         (rc = occupancy(&D.mid_blocks[1], (const void*)narrow_kernel<192, short, 1, 16>, 32,
@@ -1964,7 +1987,7 @@ int device_info(DeviceInfo** out) {
         (rc = occupancy(&D.cta_blocks, (const void*)wide_cta_kernel, kCtaThreads, kCtaSmemBytes)))
       return rc;
     for (int w = 0; w < 3; ++w)  // the int32 rows come in 16-cell groups only
-      D.narrow_blocks[0][w][0] = D.narrow_blocks[0][w][1] = D.narrow_blocks[0][w][2];
+      D.narrow_blocks[0][w][0] = D.narrow_blocks[0][w][1] = D.narrow_blocks[0][w][3] = D.narrow_blocks[0][w][2];
     D.ready = true;
   }
   *out = &D;
@@ -1978,6 +2001,7 @@ int validate_schedule(const dibella_schedule_t& s) {
   if (s.narrow_split_d < 0) return DIBELLA_EINVAL;
   if (s.narrow_unroll != 0 && s.narrow_unroll != 4 && s.narrow_unroll != 8 && s.narrow_unroll != 16)
     return DIBELLA_EINVAL;
+  if (s.narrow_track != 0 && s.narrow_track != 1) return DIBELLA_EINVAL;
   if (s.wide_slots != 0 && s.wide_slots != 8 && s.wide_slots != 16 && s.wide_slots != 24 && s.wide_slots != 32)
     return DIBELLA_EINVAL;
   if (s.wide_slots == 8 && s.wide_group_lanes != 0 && s.wide_group_lanes != 32) return DIBELLA_EINVAL;
@@ -2025,8 +2049,13 @@ void record(cudaStream_t st, int idx) {
 // int16 narrow cells (relative scores) when X allows, else int32.
 inline int narrow_kind(int xdrop) { return xdrop <= kNarrow16MaxX ? 1 : 0; }
 
-// Index of a schedule's narrow cell group width (narrow_unroll 0 means 16).
-inline int unroll_index(int u) { return u == 4 ? 0 : (u == 8 ? 1 : 2); }
+// Index of a schedule's narrow-form variant: cell groups of 4, 8 or 16
+// (narrow_unroll 0 means 16), or 16 with the live range tracked (narrow_track;
+// int16 rows only).
+inline int narrow_variant(int unroll, int track, int xdrop) {
+  if (track && xdrop <= 8000) return 3;
+  return unroll == 4 ? 0 : (unroll == 8 ? 1 : 2);
+}
 
 template <int WT, int U>
 void launch_narrow16(int grid, cudaStream_t st, const ExtendParams& ep) {
@@ -2034,8 +2063,11 @@ void launch_narrow16(int grid, cudaStream_t st, const ExtendParams& ep) {
 }
 
 template <int WT>
-void launch_narrow16_u(int unroll, int grid, cudaStream_t st, const ExtendParams& ep) {
-  if (unroll == 4)
+void launch_narrow16_u(int unroll, bool track, int grid, cudaStream_t st, const ExtendParams& ep) {
+  if (track)  // 16-cell groups with the live range and maximum tracked in registers
+    narrow_kernel<WT, short, kWarpsPerBlock, 16, true>
+        <<<grid, kBlockThreads, narrow_smem<WT, short, kWarpsPerBlock>(), st>>>(ep);
+  else if (unroll == 4)
     launch_narrow16<WT, 4>(grid, st, ep);
   else if (unroll == 8)
     launch_narrow16<WT, 8>(grid, st, ep);
@@ -2043,14 +2075,15 @@ void launch_narrow16_u(int unroll, int grid, cudaStream_t st, const ExtendParams
     launch_narrow16<WT, 16>(grid, st, ep);
 }
 
-cudaError_t launch_narrow(int wt, int unroll, int xdrop, int grid, cudaStream_t st, const ExtendParams& ep) {
+cudaError_t launch_narrow(int wt, int unroll, bool track, int xdrop, int grid, cudaStream_t st,
+                          const ExtendParams& ep) {
   if (narrow_kind(xdrop)) {
     if (wt == 32)
-      launch_narrow16_u<32>(unroll, grid, st, ep);
+      launch_narrow16_u<32>(unroll, track, grid, st, ep);
     else if (wt == 48)
-      launch_narrow16_u<48>(unroll, grid, st, ep);
+      launch_narrow16_u<48>(unroll, track, grid, st, ep);
     else
-      launch_narrow16_u<64>(unroll, grid, st, ep);
+      launch_narrow16_u<64>(unroll, track, grid, st, ep);
   } else {
     if (wt == 32)
       narrow_kernel<32, int, kWarpsPerBlock, 16><<<grid, kBlockThreads, narrow_smem<32, int, kWarpsPerBlock>(), st>>>(ep);
@@ -2193,7 +2226,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   const int wt = sch.narrow_band_cap;
   const int vi = wt == 32 ? 0 : (wt == 48 ? 1 : 2);
   const int unroll = sch.narrow_unroll == 0 ? 16 : sch.narrow_unroll;
-  int nb = D.narrow_blocks[narrow_kind(xdrop)][vi][unroll_index(unroll)];
+  const bool track = sch.narrow_track != 0;
+  int nb = D.narrow_blocks[narrow_kind(xdrop)][vi][narrow_variant(unroll, sch.narrow_track, xdrop)];
   if (sch.narrow_blocks_per_sm > 0) nb = std::min(nb, sch.narrow_blocks_per_sm);
   cudaError_t e;
 
@@ -2207,7 +2241,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wclock = clock_for(1, D.sms * nb * kWarpsPerBlock, st);
   ep.narrow_max_d = sch.narrow_split_d;
   ep.long_q = q[kQLong];
-  if ((e = launch_narrow(wt, unroll, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch");
+  if ((e = launch_narrow(wt, unroll, track, xdrop, D.sms * nb, st, ep)) != cudaSuccess)
+    return cuda_fail(e, "narrow launch");
   ep.wclock = nullptr;
   ep.narrow_max_d = 0;
   record(st, 2);
@@ -2215,7 +2250,8 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
     ep.narrow_q = q[kQLong];
     ep.narrow_q_id = kQLong;
     ep.wclock = clock_for(5, D.sms * nb * kWarpsPerBlock, st);
-    if ((e = launch_narrow(wt, unroll, xdrop, D.sms * nb, st, ep)) != cudaSuccess) return cuda_fail(e, "narrow launch 2");
+    if ((e = launch_narrow(wt, unroll, track, xdrop, D.sms * nb, st, ep)) != cudaSuccess)
+      return cuda_fail(e, "narrow launch 2");
     ep.wclock = nullptr;
   }
   record(st, 3);
@@ -2443,7 +2479,8 @@ int dibella_xdrop_batch(const uint32_t* packed_words, const int64_t* read_word_o
     const long long narrow_lanes =
         (long long)D->sms *
         D->narrow_blocks[narrow_kind(scoring.xdrop)][wt == 32 ? 0 : (wt == 48 ? 1 : 2)]
-                        [unroll_index(sch.narrow_unroll == 0 ? 16 : sch.narrow_unroll)] *
+                        [narrow_variant(sch.narrow_unroll == 0 ? 16 : sch.narrow_unroll, sch.narrow_track,
+                                        scoring.xdrop)] *
         kBlockThreads;
     if (2 * 2 * n_pairs < 3 * narrow_lanes) sch.narrow_max_xdrop = -1;
     else if (scoring.xdrop > 10)
@@ -2726,6 +2763,12 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       c.narrow_unroll = unrolls[ui];
       rc = consider(c);
     }
+  }
+  // Stage 1e: the narrow form's live range tracked in registers or found by scans.
+  if (rc == DIBELLA_OK) {
+    dibella_schedule_t c = cur;
+    c.narrow_track = cur.narrow_track ? 0 : 1;
+    rc = consider(c);
   }
   // Stage 2: lanes per extension (warp or 16/8-lane groups) x register slots of the wide form.
   {

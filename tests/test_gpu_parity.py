@@ -34,7 +34,8 @@ def test_c1_all_pairs(c1, X):
     assert ((got["status"] & 4) != 0).sum() == len(workloads.pair_groups(c1.pairs)) - 1
 
 
-@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "unroll4", "unroll8", "split16", "split64",
+@pytest.mark.parametrize("form", ["narrow32", "narrow48", "narrow64", "unroll4", "unroll8", "track32", "track48",
+                                  "split16", "split64",
                                   "mid128", "mid192", "mid256", "nomid",
                                   "packed8", "packed16", "packed24", "packed32",
                                   "int16", "int32", "grp16x16", "grp16x24", "grp16x32", "grp8x16", "grp8x24"])
@@ -54,6 +55,9 @@ def test_every_kernel_form_matches(c1, form, X):
     elif form.startswith("unroll"):
         # the narrow band walked in groups of 4 or 8 cells (32-cell rows: more escalations too)
         sched = schedule(narrow_band_cap=32, narrow_unroll=int(form[6:]), **NARROW_ALL)
+    elif form.startswith("track"):
+        # the live range and maximum kept in registers during the band walk
+        sched = schedule(narrow_band_cap=int(form[5:]), narrow_track=1, **NARROW_ALL)
     elif form.startswith("split"):
         # the narrow form in two passes, the first stopping at antidiagonal 16 or 64
         sched = schedule(narrow_split_d=int(form[5:]), **NARROW_ALL)
@@ -125,6 +129,7 @@ def test_fuzz_medium(scoring):
                       schedule(narrow_band_cap=32, mid_band_cap=128, **NARROW_ALL),
                       schedule(mid_band_cap=0, **NARROW_ALL), schedule(narrow_split_d=40, **NARROW_ALL),
                       schedule(narrow_unroll=4, **NARROW_ALL), schedule(narrow_unroll=8, narrow_split_d=64, **NARROW_ALL),
+                      schedule(narrow_track=1, **NARROW_ALL),
                       schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, wide_group_lanes=32, **WIDE_ALL),
                       schedule(wide_group_lanes=16, **WIDE_ALL), schedule(wide_group_lanes=8, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
