@@ -932,11 +932,14 @@ __global__ void __launch_bounds__(kBlockThreads) wide_reg_kernel(ExtendParams p)
 // little faster than the unconstrained 8, and than 10 or 12, where the slot
 // code recomputes values it can no longer keep in registers), 6 for 16 slots,
 // 4 for 24 slots (c3: 14% faster than the unconstrained 3, without spills).
-template <int NC>
+// The per-warp clock is a separate instantiation (CLOCK), launched only for a
+// clocked batch: even two untaken clock branches at entry and exit changed this
+// kernel's code enough to cost 5% on the E. coli-sized escalations.
+template <int NC, bool CLOCK = false>
 __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (NC == 24 ? 4 : 1)))
     wide_pk_kernel(ExtendParams p) {
   const int lane = threadIdx.x & 31;
-  warp_clock(p.wclock, 0);
+  if (CLOCK) warp_clock(p.wclock, 0);
   const unsigned tail = *((volatile unsigned*)&p.cnt->tail[p.wide_q_id]);
   const bool fwd = NC > 8 && tail <= p.forward_max;  // 8 slots is never a ladder rung
   for (;;) {
@@ -964,7 +967,7 @@ __global__ void __launch_bounds__(kBlockThreads, NC == 8 ? 9 : (NC == 16 ? 6 : (
     }
     __syncwarp();
   }
-  warp_clock(p.wclock, 1);
+  if (CLOCK) warp_clock(p.wclock, 1);
 }
 
 // Grouped packed form: a warp runs NG = 32/GL extensions at once, GL lanes
@@ -2110,30 +2113,6 @@ cudaError_t launch_mid(const DeviceInfo& D, int wt, cudaStream_t st, const Exten
   return cudaGetLastError();
 }
 
-// Resident blocks per SM of the wide form launch_wide would run.
-int wide_blocks(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop) {
-  dibella_schedule_t sch = sch_in;
-  const bool packed = sch.wide_packed && xdrop <= kPackedMaxX;
-  int lanes = sch.wide_group_lanes;
-  if (lanes == 0) lanes = 32;
-  if (!packed) lanes = 32;
-  if (sch.wide_slots == 0) sch.wide_slots = (lanes == 32 && packed) ? (xdrop <= 30 ? 8 : 24) : (xdrop <= 30 ? 16 : 24);
-  if (lanes == 8 && sch.wide_slots == 32) sch.wide_slots = 24;
-  if (sch.wide_slots == 8 && (lanes != 32 || !packed)) sch.wide_slots = 16;
-  const int vi = sch.wide_slots == 8 ? 3 : (sch.wide_slots == 16 ? 0 : (sch.wide_slots == 24 ? 1 : 2));
-  int b;
-  if (!packed)
-    b = D.reg_blocks[sch.wide_slots == 16 ? 0 : 1];
-  else if (lanes == 32)
-    b = D.pk_blocks[vi];
-  else if (lanes == 16)
-    b = D.grp16_blocks[vi];
-  else
-    b = D.grp8_blocks[vi];
-  if (sch.wide_blocks_per_sm > 0) b = std::min(b, sch.wide_blocks_per_sm);
-  return b;
-}
-
 // The wide form of a schedule: packed int16 pairs when allowed, else int32.
 cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, int xdrop, cudaStream_t st,
                         const ExtendParams& ep) {
@@ -2163,14 +2142,19 @@ cudaError_t launch_wide(const DeviceInfo& D, const dibella_schedule_t& sch_in, i
     else
       wide_reg_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
   } else if (lanes == 32) {
+    const bool clk = ep.wclock != nullptr;
     if (vi == 3)
-      wide_pk_kernel<8><<<grid, kBlockThreads, 0, st>>>(ep);
+      clk ? wide_pk_kernel<8, true><<<grid, kBlockThreads, 0, st>>>(ep)
+          : wide_pk_kernel<8><<<grid, kBlockThreads, 0, st>>>(ep);
     else if (vi == 0)
-      wide_pk_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
+      clk ? wide_pk_kernel<16, true><<<grid, kBlockThreads, 0, st>>>(ep)
+          : wide_pk_kernel<16><<<grid, kBlockThreads, 0, st>>>(ep);
     else if (vi == 1)
-      wide_pk_kernel<24><<<grid, kBlockThreads, 0, st>>>(ep);
+      clk ? wide_pk_kernel<24, true><<<grid, kBlockThreads, 0, st>>>(ep)
+          : wide_pk_kernel<24><<<grid, kBlockThreads, 0, st>>>(ep);
     else
-      wide_pk_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
+      clk ? wide_pk_kernel<32, true><<<grid, kBlockThreads, 0, st>>>(ep)
+          : wide_pk_kernel<32><<<grid, kBlockThreads, 0, st>>>(ep);
   } else if (lanes == 16) {
     if (vi == 0)
       wide_grp_kernel<16, 16><<<grid, kBlockThreads, 0, st>>>(ep);
@@ -2264,7 +2248,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wide_q = q[kQWide];
   ep.wide_q_id = kQWide;
   ep.cells_idx = 1;
-  ep.wclock = clock_for(2, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
+  ep.wclock = clock_for(2, D.sms * 64, st);  // every warp an SM can hold; rows of absent warps stay 0
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch");
   ep.wclock = nullptr;
   record(st, 4);
@@ -2290,7 +2274,7 @@ int launch_extensions(const DeviceInfo& D, const dibella_schedule_t& sch_in, int
   ep.wide_q = q[esc_in];
   ep.wide_q_id = esc_in;
   ep.cells_idx = 4;
-  ep.wclock = clock_for(4, D.sms * wide_blocks(D, sch, xdrop) * kWarpsPerBlock, st);
+  ep.wclock = clock_for(4, D.sms * 64, st);
   if ((e = launch_wide(D, sch, xdrop, st, ep)) != cudaSuccess) return cuda_fail(e, "wide launch (escalations)");
   ep.wclock = nullptr;
   record(st, 6);
