@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--n-parts", type=int, default=8, help="stream mode: hash passes of the k-mer count")
     ap.add_argument("--tune-workload", default="c3_uneven", help="tune mode: workload")
     ap.add_argument("--trace-seeds", type=int, default=20000, help="traceback mode: accepted seeds traced")
+    ap.add_argument("--trace-warps-per-sm", type=int, default=24,
+                    help="traceback mode: warps (one workspace slot each) per SM; 24 fit at 80 registers")
     ap.add_argument("--tune-x", type=int, default=50, help="tune mode: X-drop")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -405,7 +407,7 @@ def mode_traceback(args):
     pick = np.sort(rng.choice(acc, size=min(args.trace_seeds, len(acc)), replace=False))
     seeds = w.pairs[pick]
     n = len(seeds)
-    lanes = min(n, 8 * torch.cuda.get_device_properties(dev).multi_processor_count)
+    lanes = min(n, args.trace_warps_per_sm * torch.cuda.get_device_properties(dev).multi_processor_count)
     moves_words = 1 << 20
     tal = dib.Aligner(store, n, k=K, device=dev)
     tal.upload_pairs(seeds)
