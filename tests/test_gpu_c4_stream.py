@@ -10,7 +10,7 @@ identical.
 
 * test_c4_rules_scaled: every rule of the configuration on a 0.8 Mb genome,
   every record checked.
-* test_c4_full_size (runs only with DIBELLA_SLOW=1; about 40 minutes on a
+* test_c4_full_size (runs only with DIBELLA_SLOW=1; about an hour on a
   GB300): the configured 100 Mb genome.  Read blocks play the part of chunks:
   all records of two blocks of at least 4M records each, and a seeded sample
   of records from a seeded 5% of the 2,000-read blocks (their seed records in
@@ -67,7 +67,7 @@ def test_c4_rules_scaled():
     assert out["cells"] == int(exp["cells"].sum())
 
 
-@pytest.mark.skipif(os.environ.get("DIBELLA_SLOW") != "1", reason="about 40 minutes on a GB300; DIBELLA_SLOW=1")
+@pytest.mark.skipif(os.environ.get("DIBELLA_SLOW") != "1", reason="about an hour on a GB300; DIBELLA_SLOW=1")
 def test_c4_full_size():
     report = {}
     t_all = time.time()
