@@ -426,8 +426,9 @@ int dibella_traceback_workspace_bytes(int64_t n_lanes, int32_t max_read_len, int
  * each with one workspace slot, taking seeds t = w, w + n_lanes, ...)
  * re-runs both extensions with the band across its lanes, then one lane walks
  * back: meant for the seeds whose edits are wanted (accepted overlaps).
- * Sizing: n_lanes of 4 to 8 warps per SM keeps the GPU busy (e.g. 1,024 on
- * 152 SMs); moves_words must hold, per extension, 3 words per antidiagonal up
+ * Sizing: a warp walking one seed is latency bound, so give it occupancy:
+ * 24 warps per SM (3,648 on 152 SMs; 80 registers per thread) traced twice
+ * as many seeds per second as 8; moves_words must hold, per extension, 3 words per antidiagonal up
  * to the best one plus 2 bits per evaluated cell, about (m + n) x (3 + band /
  * 16) words for an m x n extension (2^18 words cover a 30 kb overlap at a
  * 40-cell band).  EINVAL on the scoring limits of
