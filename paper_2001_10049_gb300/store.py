@@ -152,18 +152,21 @@ class Aligner:
         from . import RESULT_DTYPE
         return self.results[:n_pairs].cpu().numpy().reshape(-1).view(RESULT_DTYPE)
 
-    def traceback(self, pairs: np.ndarray, scoring, ops_per_seed: int = 4096, n_lanes: int = 1024,
+    def traceback(self, pairs: np.ndarray, scoring, ops_per_seed: int = 4096, n_lanes: int | None = None,
                   moves_words: int = 1 << 18):
         """The seeds' results and the run-length encoded columns of their best
         alignments (dibella_xdrop_traceback; synchronous): (results,
-        ops[n, ops_per_seed] uint32, n_ops[n] int32).  Scratch: n_lanes slots
-        of 3 x (longest read + 2) int32 plus moves_words words."""
+        ops[n, ops_per_seed] uint32, n_ops[n] int32).  Scratch: n_lanes warp
+        slots (default 24 per SM, where one warp per seed is no longer latency
+        bound) of 3 x (longest read + 2) int32 plus moves_words words."""
         from . import RESULT_DTYPE, Scoring, dibella_traceback_workspace_bytes, dibella_xdrop_traceback
         torch = _torch()
         s = scoring if isinstance(scoring, Scoring) else Scoring(*scoring)
         n = self.upload_pairs(pairs)
         ops = torch.zeros((max(n, 1), ops_per_seed), dtype=torch.int32, device=self.device)
         n_ops = torch.zeros(max(n, 1), dtype=torch.int32, device=self.device)
+        if n_lanes is None:
+            n_lanes = 24 * torch.cuda.get_device_properties(self.device).multi_processor_count
         lanes = max(1, min(n_lanes, n))
         st = self.store
         ws_bytes = dibella_traceback_workspace_bytes(lanes, max(st.max_len, 1), moves_words)
