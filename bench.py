@@ -613,10 +613,11 @@ def cand_bytes_per_pair(passes: int) -> int:
     return 8 + 24 * passes + 16
 
 
-# DRAM bytes of one call (every kernel of the call, from one ncu launch list)
-# for kernels unchanged since that capture; none is current: the radix passes
-# moved from 16,384- to 8,192-key tiles after the capture in
-# profiles/candidate_pairs_c2_ecoli_launch_list.md (25,658,249,318 B then).
+# DRAM bytes of one call (every kernel of the call, from one ncu capture) for
+# kernels unchanged since that capture; none is current: the radix passes moved
+# from 16,384- to 8,192-key tiles after the last DRAM capture (25,658,249,318 B
+# per call then), and the current launch list
+# (profiles/candidate_pairs_c2_ecoli_launch_list.md) holds durations only.
 CAND_NCU_TRAFFIC = {}
 
 
