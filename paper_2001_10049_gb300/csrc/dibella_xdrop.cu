@@ -685,21 +685,21 @@ __device__ bool extend_pk(const uint32_t* __restrict__ words, const Item& it, co
     if (last_rel < 0) break;
     const int first = 64 * cbase + first_rel, last = 64 * cbase + last_rel;
     if (vrel + rb > best) {
-      const int sl = first_rel >> 6, sh = last_rel >> 6;
+      // Smallest i holding the new best: each lane's smallest matching cell
+      // over slots 1..sh, then one warp minimum.  Slots below the live range's
+      // are dead on this antidiagonal (every cell holds kNeg16), so they never
+      // match; slots above sh are not scanned (they may hold older values).
+      const int sh = last_rel >> 6;
       const unsigned v2 = pk_pair(vrel, vrel);
-      int cand = INT32_MAX;
+      int my_c = INT32_MAX;
 #pragma unroll
       for (int s = 1; s < NC; ++s) {
         if (s > sh) break;
-        if (s >= sl) {
-          const unsigned e = H[s] ^ v2;
-          const unsigned blo = __ballot_sync(kFull, (e & 0xFFFFu) == 0);
-          const unsigned bhi = __ballot_sync(kFull, (e >> 16) == 0);
-          const int f0 = blo ? 2 * (__ffs(blo) - 1) : INT32_MAX;
-          const int f1 = bhi ? 2 * (__ffs(bhi) - 1) + 1 : INT32_MAX;
-          if (min(f0, f1) != INT32_MAX) cand = min(cand, 64 * (cbase + s) + min(f0, f1));
-        }
+        const unsigned e = H[s] ^ v2;
+        const int c = 64 * s + 2 * lane;
+        my_c = min(my_c, (e & 0xFFFFu) == 0 ? c : ((e >> 16) == 0 ? c + 1 : INT32_MAX));
       }
+      const int cand = 64 * cbase + __reduce_min_sync(kFull, my_c);
       best = vrel + rb;
       bi = cand;
       bj = d - cand;
@@ -842,7 +842,7 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
           const int lf = p1[t * 32];
           const int dn = p2[t * 32];
           const int sub = ((mg >> (2 * t)) & 1u) ? sc.S : sc.M;
-          int h = max(max(u, lf) + sc.G, dg + sub);
+          int h = __viaddmax_s32(max(u, lf), sc.G, dg + sub);  // max(max(u, lf) + G, dg + sub)
           h = h >= thr ? h : kD;
           p2[t * 32] = (T)h;
           if (TRACK) {
