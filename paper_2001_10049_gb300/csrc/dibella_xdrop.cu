@@ -836,11 +836,25 @@ __device__ int narrow_step(NarrowLane<WT>& L, const uint32_t* __restrict__ words
       T* p1 = &nslot<WT>(wbase, h1, i + g - f, lane);
       T* p2 = &nslot<WT>(wbase, h2, i + g - f, lane);
       const uint32_t mg = mm >> (2 * g);
+      // Four cells at a time: their d-1 and d-2 values are loaded before any of
+      // them is stored.  The compiler cannot tell that the two rows never
+      // overlap, so a load of row d-1 issued after a store to row d-2 would wait
+      // for it, and each cell would wait out a shared-memory latency.
+      int lfv[U], dnv[U];
 #pragma unroll
       for (int t = 0; t < U; ++t) {
+        if ((t & 3) == 0) {
+#pragma unroll
+          for (int k = t; k < t + 4; ++k) {
+            if (g + k < cnt) {
+              lfv[k] = p1[k * 32];
+              dnv[k] = p2[k * 32];
+            }
+          }
+        }
         if (g + t < cnt) {
-          const int lf = p1[t * 32];
-          const int dn = p2[t * 32];
+          const int lf = lfv[t];
+          const int dn = dnv[t];
           const int sub = ((mg >> (2 * t)) & 1u) ? sc.S : sc.M;
           int h = __viaddmax_s32(max(u, lf), sc.G, dg + sub);  // max(max(u, lf) + G, dg + sub)
           h = h >= thr ? h : kD;
