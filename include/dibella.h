@@ -171,9 +171,10 @@ typedef struct {
                                   /* first stopping at this antidiagonal      */
   int32_t narrow_unroll;          /* narrow form: cells per unrolled group of */
                                   /* its band walk, 4, 8 or 16 (0 = 16)       */
-  int32_t narrow_track;           /* 1: narrow form keeps its live range and  */
-                                  /* maximum in registers while it walks the  */
-                                  /* band (16-cell groups, int16 rows), 0:    */
+  int32_t narrow_track;           /* 1 (the default's): narrow form keeps its */
+                                  /* live range and maximum in registers while*/
+                                  /* it walks the band (16-cell groups, int16 */
+                                  /* rows; narrow_unroll is then ignored), 0: */
                                   /* finds them by scans of the new row       */
 } dibella_schedule_t;
 
@@ -449,8 +450,8 @@ int dibella_xdrop_traceback(const uint32_t* packed_words, const int64_t* read_wo
  * The search is staged: routing threshold between the one-thread and the
  * wide forms x per-thread band chunk (32/48/64), then the mid form's band
  * (none/128/192/256), the split of the narrow form (none/64/128/256
- * antidiagonals), its cell groups (4/8/16) and its live-range tracking,
- * then lanes per extension
+ * antidiagonals), its band walk (cell groups of 4/8/16 with scans of the
+ * new row, or 16 with the live range tracked), then lanes per extension
  * (32/16/8) x register slots (16/24/32) of the wide form, then resident
  * blocks per SM, then length-bucket bounds; each stage keeps the best so
  * far.  Same arguments as

@@ -1844,7 +1844,7 @@ dibella_schedule_t g_default_schedule = {
     /*wide_slots=*/0, /*wide_packed=*/1, /*wide_group_lanes=*/0, /*wide_blocks_per_sm=*/0,
     /*narrow_blocks_per_sm=*/0,
     /*n_buckets=*/6, {500, 2000, 5000, 10000, 20000, 0, 0, 0}, /*mid_band_cap=*/0, /*narrow_split_d=*/0,
-    /*narrow_unroll=*/0, /*narrow_track=*/0};
+    /*narrow_unroll=*/0, /*narrow_track=*/1};
 
 struct DeviceInfo {
   bool ready = false;
@@ -2751,22 +2751,19 @@ int dibella_autotune(const uint32_t* packed_words, const int64_t* read_word_offs
       rc = consider(c);
     }
   }
-  // Stage 1d: the narrow form's cell groups (4, 8 or 16 cells).
+  // Stage 1d: the narrow form's band walk: groups of 4, 8 or 16 cells with the
+  // live range found by scans of the new row, or 16 with it tracked in registers.
   {
     const dibella_schedule_t base1d = cur;
-    const int unrolls[3] = {4, 8, 16};
-    for (int ui = 0; ui < 3 && rc == DIBELLA_OK; ++ui) {
-      if (unrolls[ui] == (base1d.narrow_unroll == 0 ? 16 : base1d.narrow_unroll)) continue;
+    const int unrolls[4] = {4, 8, 16, 16}, tracks[4] = {0, 0, 0, 1};
+    const int cur_u = base1d.narrow_unroll == 0 ? 16 : base1d.narrow_unroll;
+    for (int vi = 0; vi < 4 && rc == DIBELLA_OK; ++vi) {
+      if (tracks[vi] == base1d.narrow_track && (tracks[vi] != 0 || unrolls[vi] == cur_u)) continue;
       dibella_schedule_t c = base1d;
-      c.narrow_unroll = unrolls[ui];
+      c.narrow_unroll = unrolls[vi];
+      c.narrow_track = tracks[vi];
       rc = consider(c);
     }
-  }
-  // Stage 1e: the narrow form's live range tracked in registers or found by scans.
-  if (rc == DIBELLA_OK) {
-    dibella_schedule_t c = cur;
-    c.narrow_track = cur.narrow_track ? 0 : 1;
-    rc = consider(c);
   }
   // Stage 2: lanes per extension (warp or 16/8-lane groups) x register slots of the wide form.
   {

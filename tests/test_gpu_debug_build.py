@@ -28,8 +28,9 @@ dib.dibella_bounds_check(reset=True)
 out = {"cases": 0, "mismatch": []}
 for X in (0, 7, 25, 1 << 30):
     exp = oracle_align(w.reads, w.offsets, w.pairs, 17, (1, -1, -1, X))
-    for name, sch in (("default", None), ("narrow32", schedule(narrow_band_cap=32, **NARROW_ALL)),
-                      ("mid128", schedule(narrow_band_cap=32, mid_band_cap=128, **NARROW_ALL)),
+    for name, sch in (("default", None), ("narrow32", schedule(narrow_band_cap=32, narrow_track=0, **NARROW_ALL)),
+                      ("track32", schedule(narrow_band_cap=32, narrow_track=1, **NARROW_ALL)),
+                      ("mid128", schedule(narrow_band_cap=32, mid_band_cap=128, narrow_track=0, **NARROW_ALL)),
                       ("wide", schedule(**WIDE_ALL)), ("int32", schedule(wide_packed=0, **WIDE_ALL))):
         got = al.align(w.pairs, dib.Scoring(1, -1, -1, X), sched=sch)
         out["cases"] += 1
@@ -51,6 +52,6 @@ def test_debug_build_is_clean_and_exact():
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT], env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stderr[-3000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
-    assert out["is_debug"] and out["cases"] == 20
+    assert out["is_debug"] and out["cases"] == 24  # 4 X values x 6 schedules
     assert out["mismatch"] == []
     assert out["record"] == {"code": 0, "index": 0, "limit": 0, "count": 0}, out["record"]

@@ -51,20 +51,21 @@ def test_every_kernel_form_matches(c1, form, X):
         sched = schedule(wide_slots=int(form[3:]), wide_packed=0, **WIDE_ALL)
     elif form.startswith("mid"):
         # every extension through the 32-cell narrow form, its escalations through the mid form
-        sched = schedule(narrow_band_cap=32, mid_band_cap=int(form[3:]), **NARROW_ALL)
+        sched = schedule(narrow_band_cap=32, mid_band_cap=int(form[3:]), narrow_track=0, **NARROW_ALL)
     elif form.startswith("unroll"):
         # the narrow band walked in groups of 4 or 8 cells (32-cell rows: more escalations too)
-        sched = schedule(narrow_band_cap=32, narrow_unroll=int(form[6:]), **NARROW_ALL)
+        sched = schedule(narrow_band_cap=32, narrow_unroll=int(form[6:]), narrow_track=0, **NARROW_ALL)
     elif form.startswith("track"):
         # the live range and maximum kept in registers during the band walk
         sched = schedule(narrow_band_cap=int(form[5:]), narrow_track=1, **NARROW_ALL)
     elif form.startswith("split"):
         # the narrow form in two passes, the first stopping at antidiagonal 16 or 64
-        sched = schedule(narrow_split_d=int(form[5:]), **NARROW_ALL)
+        sched = schedule(narrow_split_d=int(form[5:]), narrow_track=0, **NARROW_ALL)
     elif form == "nomid":
-        sched = schedule(narrow_band_cap=32, mid_band_cap=0, **NARROW_ALL)
+        sched = schedule(narrow_band_cap=32, mid_band_cap=0, narrow_track=0, **NARROW_ALL)
     else:
-        sched = schedule(narrow_band_cap=int(form[6:]), **NARROW_ALL)
+        # the band walked in 16-cell groups, live range and maximum found by scans of the row
+        sched = schedule(narrow_band_cap=int(form[6:]), narrow_track=0, **NARROW_ALL)
     pairs = c1.pairs[:300]
     sc = (1, -1, -1, X)
     got = gpu_align(c1.reads, c1.offsets, pairs, 17, sc, sched=sched)
@@ -126,10 +127,12 @@ def test_fuzz_medium(scoring):
         sc = scoring + (X,)
         exp = oracle_align(ascii, offs, pairs, k, sc)
         for sched in (None, schedule(**NARROW_ALL), schedule(**WIDE_ALL),
-                      schedule(narrow_band_cap=32, mid_band_cap=128, **NARROW_ALL),
-                      schedule(mid_band_cap=0, **NARROW_ALL), schedule(narrow_split_d=40, **NARROW_ALL),
-                      schedule(narrow_unroll=4, **NARROW_ALL), schedule(narrow_unroll=8, narrow_split_d=64, **NARROW_ALL),
-                      schedule(narrow_track=1, **NARROW_ALL),
+                      schedule(narrow_band_cap=32, mid_band_cap=128, narrow_track=0, **NARROW_ALL),
+                      schedule(mid_band_cap=0, narrow_track=0, **NARROW_ALL),
+                      schedule(narrow_split_d=40, narrow_track=0, **NARROW_ALL),
+                      schedule(narrow_unroll=4, narrow_track=0, **NARROW_ALL),
+                      schedule(narrow_unroll=8, narrow_split_d=64, narrow_track=0, **NARROW_ALL),
+                      schedule(narrow_track=0, **NARROW_ALL), schedule(narrow_track=1, **NARROW_ALL),
                       schedule(wide_packed=0, **WIDE_ALL), schedule(wide_slots=16, wide_group_lanes=32, **WIDE_ALL),
                       schedule(wide_group_lanes=16, **WIDE_ALL), schedule(wide_group_lanes=8, **WIDE_ALL)):
             got = gpu_align(ascii, offs, pairs, k, sc, sched=sched)
