@@ -267,6 +267,18 @@ def cpu_baseline(w, seconds: float, xdrops):
                       % (n_cand, len(sample), w.name, ",".join(map(str, xdrops)), threads, dt)}
 
 
+L2_NOTE = "flushed (256 MiB write) before every timed GPU batch"
+
+
+def workload_config(w, n_cand, n_seeds, xdrops, note=""):
+    """The workload a bench line measures.  Both arms of the default command
+    (the GPU batch and the host oracle) print this same dict; how an arm runs
+    it goes elsewhere in its line."""
+    return {"workload": w.name + note, "genome_bp": w.params["genome_len"], "coverage": w.params["coverage"],
+            "reads": int(w.n_reads), "candidate_pairs": int(n_cand), "seed_records": int(n_seeds),
+            "xdrop": list(xdrops), "scoring": "+1/-1/-1", "k": K, "l2": L2_NOTE}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -291,8 +303,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": "aligned pairs/s", "value": value, "unit": "aligned pairs/s",
         "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": 1000 * dt / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + " (sampled)", "xdrop": list(XDROPS),
-                                        "scoring": "+1/-1/-1", "k": K},
+        "data": "synthetic",
+        "config": workload_config(w, len(workloads.pair_groups(w.pairs)) - 1, len(w.pairs), XDROPS),
         "cpu_baseline": {"value": value, "unit": "aligned pairs/s", "cores": threads, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "aligned pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -998,17 +1010,14 @@ def main():
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": w.name + (" (sample of %d pairs)" % n_cand if args.sample_pairs else "")
-                               + (" (read_a in %s)" % args.read_ranges if args.read_ranges else ""),
-                   "genome_bp": w.params["genome_len"], "coverage": w.params["coverage"],
-                   "reads": int(w.n_reads), "candidate_pairs": n_cand, "seed_records": n_seeds,
-                   "xdrop": list(XD), "scoring": "+1/-1/-1", "k": K,
-                   "schedule": (sched or dib.dibella_get_default_schedule()).as_dict(),
-                   "l2": "flushed (256 MiB write) before every timed batch",
-                   "graph": "one CUDA graph per X (whole dibella_xdrop_batch)",
-                   "parallelism": ("cost-balanced shard of one batch" if shard_info else "replica per GPU")
-                                  if world > 1 else "1 GPU",
-                   "shard": shard_info},
+        "config": workload_config(w, n_cand, n_seeds, XD,
+                                  (" (sample of %d pairs)" % n_cand if args.sample_pairs else "")
+                                  + (" (read_a in %s)" % args.read_ranges if args.read_ranges else "")),
+        "run": {"schedule": (sched or dib.dibella_get_default_schedule()).as_dict(),
+                "graph": "one CUDA graph per X (whole dibella_xdrop_batch)",
+                "parallelism": ("cost-balanced shard of one batch" if shard_info else "replica per GPU")
+                               if world > 1 else "1 GPU",
+                "shard": shard_info},
         "gcups": total_cells / (my_ms * 1e-3) / 1e9,
         "per_xdrop": {str(X): {"ms": batch_ms[X], "pairs_per_s": n_cand / (batch_ms[X] * 1e-3),
                                "gcups": cells[X] / (batch_ms[X] * 1e-3) / 1e9, "cells": cells[X],
